@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the D3Q19 BGK hot path on GB300.
+
+Default workload: fully periodic 384^3 lattice, FP32 storage of f_i - w_i,
+tau = 0.8, initial shear wave u_x = 0.01 sin(2 pi z / N) at rho = 1 from
+equilibrium. One benchmark step = one fused pull stream-and-collide update of
+every node (one kernel launch). Metric: MLUPS (million lattice updates per
+second, Sec. 1 footnote), plus the fraction of the measured HBM bandwidth
+under the byte model of Sec. 4.1 (152 B per update in FP32).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica on its own GPU (the
+lattice does not shard in this build); rank 0 prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT = 384
+TAU = 0.8
+AMP = 0.01
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N_DEFAULT, help="lattice edge (cube)")
+    p.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
+    p.add_argument("--e2e-calls", type=int, default=5)
+    p.add_argument("--cpu-sample-n", type=int, default=128)
+    p.add_argument("--cpu-sample-steps", type=int, default=20)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_1309_1983_gb300/csrc/lbm_step.cu", "paper_1309_1983_gb300/csrc/d3q19.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(summary_name):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    summary is missing or was taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", summary_name)
+    try:
+        kv = {}
+        with open(path) as fh:
+            for line in fh:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch_scaled"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.out = os.path.join("/tmp", f"lbm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.fh = open(self.out, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.out):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    sm.append(float(parts[2]))
+                    mx = float(parts[3])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[6:10]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.remove(self.out)
+        except Exception:
+            pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(n, steps):
+    """The FP64 oracle as it stands, on this host's cores, over a bounded
+    sample: a periodic n^3 shear-wave lattice (the same workload, smaller),
+    ``steps`` updates. Returns MLUPS and the thread count."""
+    import oracle as O
+    from paper_1309_1983_gb300 import workloads as W
+    L = O.Lattice(n, n, n, TAU)
+    f = O.init_equilibrium(L, None, W.shear_wave(n, n, n, AMP))
+    O.run(L, f, 1)  # warm the pages and the thread pool
+    t0 = time.perf_counter()
+    O.run(L, f, steps)
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt / 1e6, O.max_threads(), dt
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_1309_1983_gb300 import workloads as W
+    n = 64
+    L = O.Lattice(n, n, n, TAU)
+    f = O.init_equilibrium(L, None, W.shear_wave(n, n, n, AMP))
+    for _ in range(args.warmup):
+        f = O.run(L, f, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        f = O.run(L, f, 1)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    mlups = n ** 3 * args.steps / total / 1e6
+    sample = (f"FP64 oracle, one update of a periodic {n}^3 shear-wave lattice per step "
+              f"(bounded sample of the {args.n}^3 workload; same per-node arithmetic)")
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"d3q19_periodic_shear_wave_{args.n}^3", "tau": TAU,
+                   "sample_lattice": f"{n}^3", "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": O.max_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def timed_steps(L, steps, torch):
+    """Time ``steps`` single-update launches with CUDA events on the
+    library's stream; returns (total ms, per-step ms list)."""
+    s = L.stream
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    evs[0].record(s)
+    for k in range(steps):
+        L.step(1)
+        evs[k + 1].record(s)
+    s.synchronize()
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    return evs[0].elapsed_time(evs[-1]), per
+
+
+def extra_workloads(torch, n, steps=100, warmup=10):
+    """Secondary workloads of the same hot path, each timed like the main
+    one: the paper's lid-driven cavity (FP32) and 16-bit storage."""
+    from paper_1309_1983_gb300.lattice import Lattice
+    from paper_1309_1983_gb300 import perfmodel as PM
+    out = {}
+    for name, storage, tau in (("cavity_f32", "f32", 0.55), ("cavity_f16", "f16", 0.55),
+                               ("cavity_bf16", "bf16", 0.55)):
+        L = Lattice(n, n, n, tau, walls=(True, True, True), lid=(0.05, 0.0, 0.0), storage=storage)
+        L.init_equilibrium()
+        L.step(warmup)
+        ms, per = timed_steps(L, steps, torch)
+        mlups = n ** 3 * steps / (ms / 1e3) / 1e6
+        eb = 4 if storage == "f32" else 2
+        out[name] = {"mlups": round(mlups, 1), "bytes_per_lu": PM.bytes_per_update(eb),
+                     "gbs": round(PM.achieved_gbs(mlups, PM.bytes_per_update(eb)), 1),
+                     "steps": steps}
+        L.close()
+        del L
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1309_1983_gb300 import build as B
+    B.build()
+    from paper_1309_1983_gb300 import capi, perfmodel as PM, workloads as W
+    from paper_1309_1983_gb300.lattice import Lattice
+    capi.load()
+
+    n = args.n
+    cells = n ** 3
+    L = Lattice(n, n, n, TAU)
+    u0 = torch.from_numpy(W.shear_wave(n, n, n, AMP)).float().cuda()
+    L.init_equilibrium(u=u0)
+    L.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(props.uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, per = timed_steps(L, args.steps, torch)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ws * cells * args.steps / (ms_max / 1e3) / 1e6
+    per_rank_mlups = cells * args.steps / (ms / 1e3) / 1e6
+    step_ms = ms / args.steps
+    mlups_each = [cells / (p / 1e3) / 1e6 for p in per]
+
+    # physics sanity on the benchmarked state: mass is conserved
+    mass = L.mass()
+    mass_rel = abs(mass / cells - 1.0)
+
+    # roofline of the dominant (only) kernel
+    bpl = PM.bytes_per_update(4)
+    peak, peak_kind = measured_hbm()
+    achieved = bpl * cells / (step_ms / 1e3) / 1e9
+    traffic = ncu_traffic("k_step_f32_periodic_384.txt") if n == 384 else None
+
+    # end to end through the C ABI on host buffers
+    u0_h = torch.from_numpy(W.shear_wave(n, n, n, AMP)).float().pin_memory()
+    rho_h = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+    u_h = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
+    L.run_host(u0_h, 1, rho_h, u_h)  # warm
+    e2e_t = []
+    for _ in range(args.e2e_calls):
+        t0 = time.perf_counter()
+        L.run_host(u0_h, 1, rho_h, u_h)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_mlups = cells / statistics.median(e2e_t) / 1e6
+
+    extras = None
+    if rank == 0 and not args.no_extras:
+        L.close()
+        del L, u0
+        torch.cuda.empty_cache()
+        extras = extra_workloads(torch, n)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    cpu = None
+    if ws == 1:
+        cm, cores, cdt = cpu_baseline(args.cpu_sample_n, args.cpu_sample_steps)
+        cpu = {"value": round(cm, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": (f"FP64 oracle, periodic {args.cpu_sample_n}^3 shear wave, "
+                          f"{args.cpu_sample_steps} updates ({cdt:.1f} s), same per-node "
+                          f"arithmetic as the {n}^3 workload")}
+
+    line = {
+        "metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"d3q19_bgk_periodic_{n}^3_fp32_shear_wave",
+                   "nx": n, "ny": n, "nz": n, "tau": TAU, "storage": "f32 (f_i - w_i)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": f"inputs larger than L2 ({2 * 19 * 4 * cells / 1e9:.2f} GB working set)",
+                   "bytes_per_update": bpl},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "kernel": "k_step<f32, periodic>",
+                     "algorithmic_bytes_per_launch": bpl * cells},
+        "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS",
+                "h2d_bytes_per_step": 3 * 4 * cells, "d2h_bytes_per_step": 4 * 4 * cells,
+                "call": "lbm_run_host(u0 host -> init -> 1 update -> rho,u host)"},
+        "gpu_launches": args.steps,
+        "per_step_mlups": {"mean": round(statistics.mean(mlups_each), 1),
+                           "stdev": round(statistics.pstdev(mlups_each), 1),
+                           "best": round(max(mlups_each), 1)},
+        "per_rank_mlups": round(per_rank_mlups, 1),
+        "mass_rel_drift": mass_rel,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "extras": extras,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,431 @@
+// lbm_capi.cu - the extern "C" entry points of liblbm.so declared in lbm.h:
+// handle management, argument checks, the ping-pong buffer swap of Sec. 4.1
+// (footnote), host exchange of states, and the launch of the kernels in
+// lbm_step.cu.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "d3q19.cuh"
+#include "internal.h"
+
+using lbm::StepArgs;
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+int fail(int code, const char *what) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s", what);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where,
+           cudaGetErrorString(e));
+  return LBM_ECUDA;
+}
+
+#define LBM_CUDA(call, where)                    \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+constexpr uint32_t kKnownFlags = LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z |
+                                 LBM_LID | LBM_STORE_F16 | LBM_STORE_BF16 |
+                                 LBM_FORCE;
+
+StepArgs make_args(const lbm_t *h, const void *fin, void *fout) {
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.fin = fin;
+  a.fout = fout;
+  a.force = (h->flags & LBM_FORCE) ? h->force : nullptr;
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.nz = h->nz;
+  a.pitch = h->pitch;
+  a.plane = (uint32_t)h->plane;
+  a.cells = (uint32_t)((size_t)h->nx * h->ny * h->nz);
+  a.omega = 1.0f / h->tau;
+  a.kf = 1.0f - 0.5f * a.omega;
+  a.walls = h->flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z);
+  for (int i = 0; i < lbm::Q; ++i) {
+    a.lidc[i] = 0.0f;
+    if ((h->flags & LBM_LID) && lbm::kEz[i] == -1)
+      a.lidc[i] = (float)(6.0 * lbm::weight_d(i) *
+                          (lbm::kEx[i] * (double)h->lid[0] +
+                           lbm::kEy[i] * (double)h->lid[1] +
+                           lbm::kEz[i] * (double)h->lid[2]));
+  }
+  return a;
+}
+
+int check_bound(const lbm_t *h) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (!h->bound) return fail(LBM_EUNBOUND, "no buffers bound");
+  return LBM_OK;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int ensure_scratch(lbm_t *h) {
+  int dev = 0;
+  LBM_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (h->scr.partials && h->device == dev) return LBM_OK;
+  if (h->scr.partials) {
+    cudaFree(h->scr.partials);
+    h->scr = lbm::Scratch();
+  }
+  // one allocation: partials | sum | err
+  const size_t bytes = sizeof(double) * (lbm::kReduceBlocks + 1) + 64;
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LBM_ENOMEM, "cudaMalloc of the handle scratch failed");
+  }
+  h->scr.partials = static_cast<double *>(p);
+  h->scr.sum = h->scr.partials + lbm::kReduceBlocks;
+  h->scr.err = reinterpret_cast<int *>(h->scr.sum + 1);
+  h->scr.nblocks = lbm::kReduceBlocks;
+  h->device = dev;
+  LBM_CUDA(cudaMemset(h->scr.err, 0, sizeof(int)), "cudaMemset");
+  return LBM_OK;
+}
+
+int do_steps(lbm_t *h, int n, float *rho, float *u) {
+  for (int k = 0; k < n; ++k) {
+    StepArgs a = make_args(h, h->f[h->cur], h->f[1 - h->cur]);
+    const bool mom = (rho != nullptr) && (k == n - 1);
+    if (mom) {
+      a.rho = rho;
+      a.u = u;
+    }
+    cudaError_t e = lbm::launch_step(h->storage, mom, a, h->bx, h->by, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+    h->cur ^= 1;
+  }
+  return LBM_OK;
+}
+
+float host_to_float(const void *base, size_t k, int storage) {
+  switch (storage) {
+    case lbm::kF16: return __half2float(static_cast<const __half *>(base)[k]);
+    case lbm::kBF16:
+      return __bfloat162float(static_cast<const __nv_bfloat16 *>(base)[k]);
+    default: return static_cast<const float *>(base)[k];
+  }
+}
+
+void host_from_float(void *base, size_t k, int storage, float v) {
+  switch (storage) {
+    case lbm::kF16: static_cast<__half *>(base)[k] = __float2half_rn(v); break;
+    case lbm::kBF16:
+      static_cast<__nv_bfloat16 *>(base)[k] = __float2bfloat16_rn(v);
+      break;
+    default: static_cast<float *>(base)[k] = v;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_EINVAL: return "LBM_EINVAL: invalid argument";
+    case LBM_ENOMEM: return "LBM_ENOMEM: allocation failed";
+    case LBM_ECUDA: return "LBM_ECUDA: CUDA error";
+    case LBM_ETIMEOUT: return "LBM_ETIMEOUT: bounded device wait gave up";
+    case LBM_ENONFINITE: return "LBM_ENONFINITE: non-finite density";
+    case LBM_EUNBOUND: return "LBM_EUNBOUND: no buffers bound";
+    case LBM_ERANGE: return "LBM_ERANGE: size above the supported maximum";
+    default: return "LBM: unknown status code";
+  }
+}
+
+const char *lbm_last_error(void) { return g_last_error; }
+
+int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
+               lbm_t **out) {
+  if (!out) return fail(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(LBM_EINVAL, "sizes must be >= 1");
+  if (!(tau > 0.5f) || !isfinite(tau)) return fail(LBM_EINVAL, "tau must be > 1/2");
+  if (flags & ~kKnownFlags) return fail(LBM_EINVAL, "unknown flag bits");
+  const uint32_t st = flags & (LBM_STORE_F16 | LBM_STORE_BF16);
+  if (st == (LBM_STORE_F16 | LBM_STORE_BF16))
+    return fail(LBM_EINVAL, "more than one storage type");
+  if ((flags & LBM_LID) && !(flags & LBM_WALL_Z))
+    return fail(LBM_EINVAL, "LBM_LID needs LBM_WALL_Z");
+  const int storage = st == LBM_STORE_F16 ? lbm::kF16
+                      : st == LBM_STORE_BF16 ? lbm::kBF16 : lbm::kF32;
+  const int eb = storage == lbm::kF32 ? 4 : 2;
+  const int align = 32 / eb;  // 32-byte rows
+  const long long pitch = ((long long)nx + align - 1) / align * align;
+  const long long plane = pitch * ny * (long long)nz;
+  if (plane >= (1ll << 31)) return fail(LBM_ERANGE, "nz*ny*pitch must be < 2^31");
+  lbm_t *h = new (std::nothrow) lbm_t();
+  if (!h) return fail(LBM_ENOMEM, "host allocation failed");
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = nz;
+  h->pitch = (int)pitch;
+  h->flags = flags;
+  h->storage = storage;
+  h->elem_bytes = eb;
+  h->plane = (size_t)plane;
+  h->tau = tau;
+  h->lid[0] = h->lid[1] = h->lid[2] = 0.0f;
+  h->f[0] = h->f[1] = nullptr;
+  h->cur = 0;
+  h->force = nullptr;
+  h->stream = nullptr;
+  h->bound = false;
+  const int bx = nx >= 128 ? 128 : ((nx + 31) / 32) * 32;
+  int by = 256 / bx;
+  if (by > ny) by = ny;
+  h->bx = bx;
+  h->by = by < 1 ? 1 : by;
+  h->device = -1;
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_destroy(lbm_t *h) {
+  if (!h) return LBM_OK;
+  if (h->scr.partials) cudaFree(h->scr.partials);
+  delete h;
+  return LBM_OK;
+}
+
+int lbm_get_layout(const lbm_t *h, lbm_layout_t *out) {
+  if (!h || !out) return fail(LBM_EINVAL, "NULL argument");
+  out->nx = h->nx;
+  out->ny = h->ny;
+  out->nz = h->nz;
+  out->pitch = h->pitch;
+  out->elem_bytes = h->elem_bytes;
+  out->plane = h->plane;
+  out->f_bytes = (size_t)lbm::Q * h->plane * h->elem_bytes;
+  // adjoint buffers are FP32 on the FP32 row alignment
+  const size_t pitch32 = ((size_t)h->nx + 7) / 8 * 8;
+  out->lambda_bytes = (size_t)lbm::Q * pitch32 * h->ny * h->nz * 4;
+  out->cells = (size_t)h->nx * h->ny * h->nz;
+  return LBM_OK;
+}
+
+int lbm_bind(lbm_t *h, void *f_a, void *f_b, const float *force, void *stream) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (!f_a || !f_b || f_a == f_b) return fail(LBM_EINVAL, "need two distinct f buffers");
+  if (!aligned(f_a, 256) || !aligned(f_b, 256))
+    return fail(LBM_EINVAL, "f buffers must be 256-byte aligned");
+  if ((h->flags & LBM_FORCE) && !force)
+    return fail(LBM_EINVAL, "LBM_FORCE needs a force field");
+  if (force && !aligned(force, 4)) return fail(LBM_EINVAL, "force misaligned");
+  int rc = ensure_scratch(h);
+  if (rc) return rc;
+  h->f[0] = f_a;
+  h->f[1] = f_b;
+  h->cur = 0;
+  h->force = force;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->bound = true;
+  return LBM_OK;
+}
+
+int lbm_set_lid(lbm_t *h, float ux, float uy, float uz) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (!(h->flags & LBM_LID)) return fail(LBM_EINVAL, "handle has no lid");
+  if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz))
+    return fail(LBM_EINVAL, "lid velocity not finite");
+  h->lid[0] = ux;
+  h->lid[1] = uy;
+  h->lid[2] = uz;
+  return LBM_OK;
+}
+
+int lbm_set_tau(lbm_t *h, float tau) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (!(tau > 0.5f) || !isfinite(tau)) return fail(LBM_EINVAL, "tau must be > 1/2");
+  h->tau = tau;
+  return LBM_OK;
+}
+
+int lbm_set_block(lbm_t *h, int bx, int by) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 256)
+    return fail(LBM_EINVAL, "block must be bx%32==0, by>=1, bx*by<=256");
+  h->bx = bx;
+  h->by = by;
+  return LBM_OK;
+}
+
+int lbm_current(const lbm_t *h, void **f_cur, void **f_other) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (f_cur) *f_cur = h->f[h->cur];
+  if (f_other) *f_other = h->f[1 - h->cur];
+  return LBM_OK;
+}
+
+int lbm_init_equilibrium(lbm_t *h, const float *rho, const float *u) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  StepArgs a = make_args(h, nullptr, h->f[h->cur]);
+  cudaError_t e = lbm::launch_init(h->storage, a, rho, u, h->bx, h->by, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "init kernel launch");
+  return LBM_OK;
+}
+
+int lbm_step(lbm_t *h, int n) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
+  return do_steps(h, n, nullptr, nullptr);
+}
+
+int lbm_step_moments(lbm_t *h, int n, float *rho, float *u) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (n < 1 || !rho || !u) return fail(LBM_EINVAL, "need n >= 1 and rho, u");
+  return do_steps(h, n, rho, u);
+}
+
+int lbm_step_to(lbm_t *h, const void *f_in, void *f_out) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (!f_in || !f_out || f_in == f_out) return fail(LBM_EINVAL, "bad buffers");
+  if (!aligned(f_in, 256) || !aligned(f_out, 256))
+    return fail(LBM_EINVAL, "f buffers must be 256-byte aligned");
+  StepArgs a = make_args(h, f_in, f_out);
+  cudaError_t e = lbm::launch_step(h->storage, false, a, h->bx, h->by, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_t *h, float *rho, float *u, double *mass) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  StepArgs a = make_args(h, nullptr, nullptr);
+  if (mass) LBM_CUDA(cudaMemsetAsync(h->scr.err, 0, sizeof(int), h->stream), "memset");
+  cudaError_t e = lbm::launch_moments(h->storage, a, h->f[h->cur], rho, u,
+                                      mass ? &h->scr : nullptr, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "moments kernel launch");
+  if (!mass) return LBM_OK;
+  e = lbm::launch_finalize_sum(h->scr, lbm::moments_blocks(a.cells),
+                               (double)a.cells, h->scr.sum, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "finalize kernel launch");
+  double m = 0.0;
+  int err = 0;
+  LBM_CUDA(cudaMemcpyAsync(&m, h->scr.sum, sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream), "mass copy");
+  LBM_CUDA(cudaMemcpyAsync(&err, h->scr.err, sizeof(int), cudaMemcpyDeviceToHost,
+                           h->stream), "error word copy");
+  LBM_CUDA(cudaStreamSynchronize(h->stream), "stream sync");
+  *mass = m;
+  if (err & lbm::kErrNonFinite) return fail(LBM_ENONFINITE, "non-finite density");
+  return LBM_OK;
+}
+
+int lbm_sync(lbm_t *h) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  LBM_CUDA(cudaStreamSynchronize(h->stream), "stream sync");
+  LBM_CUDA(cudaGetLastError(), "pending error");
+  return LBM_OK;
+}
+
+int lbm_get_f(lbm_t *h, double *host_f) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (!host_f) return fail(LBM_EINVAL, "host_f is NULL");
+  const size_t bytes = (size_t)lbm::Q * h->plane * h->elem_bytes;
+  void *stage = malloc(bytes);
+  if (!stage) return fail(LBM_ENOMEM, "host staging allocation failed");
+  cudaError_t e = cudaMemcpyAsync(stage, h->f[h->cur], bytes,
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    free(stage);
+    return cuda_fail(e, "state copy to host");
+  }
+  const size_t cells = (size_t)h->nx * h->ny * h->nz;
+  for (int i = 0; i < lbm::Q; ++i) {
+    const double w = lbm::weight_d(i);
+    for (int z = 0; z < h->nz; ++z)
+      for (int y = 0; y < h->ny; ++y)
+        for (int x = 0; x < h->nx; ++x) {
+          const size_t k = i * h->plane + ((size_t)z * h->ny + y) * h->pitch + x;
+          const size_t o = i * cells + ((size_t)z * h->ny + y) * h->nx + x;
+          host_f[o] = (double)host_to_float(stage, k, h->storage) + w;
+        }
+  }
+  free(stage);
+  return LBM_OK;
+}
+
+int lbm_set_f(lbm_t *h, const double *host_f) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (!host_f) return fail(LBM_EINVAL, "host_f is NULL");
+  const size_t bytes = (size_t)lbm::Q * h->plane * h->elem_bytes;
+  void *stage = calloc(1, bytes);
+  if (!stage) return fail(LBM_ENOMEM, "host staging allocation failed");
+  const size_t cells = (size_t)h->nx * h->ny * h->nz;
+  for (int i = 0; i < lbm::Q; ++i) {
+    const double w = lbm::weight_d(i);
+    for (int z = 0; z < h->nz; ++z)
+      for (int y = 0; y < h->ny; ++y)
+        for (int x = 0; x < h->nx; ++x) {
+          const size_t k = i * h->plane + ((size_t)z * h->ny + y) * h->pitch + x;
+          const size_t o = i * cells + ((size_t)z * h->ny + y) * h->nx + x;
+          host_from_float(stage, k, h->storage, (float)(host_f[o] - w));
+        }
+  }
+  cudaError_t e = cudaMemcpyAsync(h->f[h->cur], stage, bytes,
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  free(stage);
+  if (e != cudaSuccess) return cuda_fail(e, "state copy to device");
+  return LBM_OK;
+}
+
+int lbm_run_host(lbm_t *h, const float *u0_host, int n, float *rho_host,
+                 float *u_host) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (n < 1 || !rho_host || !u_host) return fail(LBM_EINVAL, "need n >= 1, rho, u");
+  const size_t cells = (size_t)h->nx * h->ny * h->nz;
+  // the f buffer is at least 38 * cells bytes; u0 needs 12, rho + u need 16
+  float *stage = static_cast<float *>(h->f[1 - h->cur]);
+  const float *u0d = nullptr;
+  if (u0_host) {
+    LBM_CUDA(cudaMemcpyAsync(stage, u0_host, 3 * cells * sizeof(float),
+                             cudaMemcpyHostToDevice, h->stream), "u0 copy");
+    u0d = stage;
+  }
+  rc = lbm_init_equilibrium(h, nullptr, u0d);
+  if (rc) return rc;
+  rc = do_steps(h, n, nullptr, nullptr);
+  if (rc) return rc;
+  float *rd = static_cast<float *>(h->f[1 - h->cur]);
+  float *ud = rd + cells;
+  rc = lbm_moments(h, rd, ud, nullptr);
+  if (rc) return rc;
+  LBM_CUDA(cudaMemcpyAsync(rho_host, rd, cells * sizeof(float),
+                           cudaMemcpyDeviceToHost, h->stream), "rho copy");
+  LBM_CUDA(cudaMemcpyAsync(u_host, ud, 3 * cells * sizeof(float),
+                           cudaMemcpyDeviceToHost, h->stream), "u copy");
+  LBM_CUDA(cudaStreamSynchronize(h->stream), "stream sync");
+  return LBM_OK;
+}
+
+}  // extern "C"

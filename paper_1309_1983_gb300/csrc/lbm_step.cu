@@ -1,0 +1,303 @@
+// lbm_step.cu - the forward kernels of liblbm:
+//   k_step     fused pull stream + boundary rule + collide + store (Alg. 3)
+//   k_init     f = f^eq(rho0, u0) (Eq. 5)
+//   k_moments  rho, u of a stored state (Eqs. 6-7) + FP64 mass partials
+//   k_finalize FP64 sum of the partials
+//
+// Design for sm_103a: one thread per lattice node, x-dominant blocks
+// (coalesced rows, Sec. 4.3.2 and Sec. 6), all 19 loads issued before any
+// use (ILP across the f_i, Sec. 4.3), misaligned pulls for e_x != 0 served
+// from L1/L2 with no shared-memory or shuffle staging (the DRAM-misaligned
+// variant the paper found fastest, Sec. 4.3.2), streaming (evict-first)
+// stores so the destination copy does not displace the source lines that
+// neighbouring warps still pull.
+#include "d3q19.cuh"
+#include "internal.h"
+
+namespace lbm {
+
+// Pull gather with periodic wrap on every axis. Walled axes are fixed up by
+// the caller; the wrapped loads they replace stay in bounds.
+template <int S>
+__device__ __forceinline__ void pull(const typename Store<S>::T *__restrict__ fin,
+                                     uint32_t plane, const uint32_t (&zo)[3],
+                                     const uint32_t (&yo)[3],
+                                     const uint32_t (&xo)[3], float (&d)[Q]) {
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    // source x - e_i: index [1 - e] picks (plus, same, minus) neighbour
+    const uint32_t src = zo[1 - kEz[i]] + yo[1 - kEy[i]] + xo[1 - kEx[i]];
+    d[i] = Store<S>::ld(fin + (size_t)i * plane + src);
+  });
+}
+
+// Halfway bounce-back on the walled faces touching this node:
+// g_i = f_ibar(x) + 6 w_i (e_i . u_w) when x - e_i is outside a walled axis.
+template <int S>
+__device__ __forceinline__ void bounce_back(const typename Store<S>::T *__restrict__ fin,
+                                            uint32_t plane, uint32_t c,
+                                            bool x0, bool x1, bool y0, bool y1,
+                                            bool z0, bool z1,
+                                            const float (&lidc)[Q], float (&d)[Q]) {
+  static_for<1, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    bool out = false;
+    if constexpr (kEx[i] == 1) out |= x0;
+    if constexpr (kEx[i] == -1) out |= x1;
+    if constexpr (kEy[i] == 1) out |= y0;
+    if constexpr (kEy[i] == -1) out |= y1;
+    if constexpr (kEz[i] == 1) out |= z0;
+    if constexpr (kEz[i] == -1) out |= z1;
+    if (out) {
+      float v = Store<S>::ld(fin + (size_t)kOpp[i] * plane + c);
+      // the source lies on the plane z = nz exactly when e_z = -1 at z1
+      if constexpr (kEz[i] == -1) v += z1 ? lidc[i] : 0.0f;
+      d[i] = v;
+    }
+  });
+}
+
+template <int S, bool WALLS, bool FORCE, bool MOM>
+__global__ void __launch_bounds__(256) k_step(const StepArgs a) {
+  using T = typename Store<S>::T;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const T *__restrict__ fin = static_cast<const T *>(a.fin);
+  T *__restrict__ fout = static_cast<T *>(a.fout);
+  const uint32_t row = (uint32_t)a.ny * a.pitch;
+
+  const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
+  const int zm = z == 0 ? a.nz - 1 : z - 1, zp = z == a.nz - 1 ? 0 : z + 1;
+  const uint32_t zo[3] = {zp * row, z * row, zm * row};
+  const uint32_t yo[3] = {(uint32_t)yp * a.pitch, (uint32_t)y * a.pitch,
+                          (uint32_t)ym * a.pitch};
+  const uint32_t xo[3] = {(uint32_t)xp, (uint32_t)x, (uint32_t)xm};
+  const uint32_t c = zo[1] + yo[1] + xo[1];
+
+  float d[Q];
+  pull<S>(fin, a.plane, zo, yo, xo, d);
+
+  if constexpr (WALLS) {
+    const bool x0 = (a.walls & LBM_WALL_X) && x == 0;
+    const bool x1 = (a.walls & LBM_WALL_X) && x == a.nx - 1;
+    const bool y0 = (a.walls & LBM_WALL_Y) && y == 0;
+    const bool y1 = (a.walls & LBM_WALL_Y) && y == a.ny - 1;
+    const bool z0 = (a.walls & LBM_WALL_Z) && z == 0;
+    const bool z1 = (a.walls & LBM_WALL_Z) && z == a.nz - 1;
+    if (x0 | x1 | y0 | y1 | z0 | z1)
+      bounce_back<S>(fin, a.plane, c, x0, x1, y0, y1, z0, z1, a.lidc, d);
+  }
+
+  const uint32_t dc = ((uint32_t)z * a.ny + y) * a.nx + x;
+  float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+  if constexpr (FORCE) {
+    Fx = __ldg(a.force + dc);
+    Fy = __ldg(a.force + a.cells + dc);
+    Fz = __ldg(a.force + 2 * (size_t)a.cells + dc);
+  }
+  float rho, ux, uy, uz;
+  collide<FORCE>(d, a.omega, a.kf, Fx, Fy, Fz, rho, ux, uy, uz);
+
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    Store<S>::st(fout + (size_t)i * a.plane + c, d[i]);
+  });
+  if constexpr (MOM) {
+    a.rho[dc] = rho;
+    a.u[dc] = ux;
+    a.u[a.cells + dc] = uy;
+    a.u[2 * (size_t)a.cells + dc] = uz;
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(256)
+    k_init(const StepArgs a, const float *__restrict__ rho0,
+           const float *__restrict__ u0) {
+  using T = typename Store<S>::T;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const uint32_t c = ((uint32_t)z * a.ny + y) * a.pitch + x;
+  const uint32_t dc = ((uint32_t)z * a.ny + y) * a.nx + x;
+  const float r = rho0 ? rho0[dc] : 1.0f;
+  float ux = 0.f, uy = 0.f, uz = 0.f;
+  if (u0) {
+    ux = u0[dc];
+    uy = u0[a.cells + dc];
+    uz = u0[2 * (size_t)a.cells + dc];
+  }
+  float d[Q];
+  shifted_equilibrium(r, ux, uy, uz, d);
+  T *fout = static_cast<T *>(a.fout);
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    Store<S>::st(fout + (size_t)i * a.plane + c, d[i]);
+  });
+}
+
+// Grid-stride over all nodes in dense order. Optional FP64 partial sum of
+// rho - 1 per block and the non-finite flag.
+template <int S, bool FORCE>
+__global__ void __launch_bounds__(kReduceThreads)
+    k_moments(const StepArgs a, const void *fv, float *__restrict__ rho,
+              float *__restrict__ u, double *__restrict__ partials,
+              int *__restrict__ err) {
+  using T = typename Store<S>::T;
+  const T *__restrict__ f = static_cast<const T *>(fv);
+  double acc = 0.0;
+  bool bad = false;
+  for (uint32_t dc = blockIdx.x * blockDim.x + threadIdx.x; dc < a.cells;
+       dc += gridDim.x * blockDim.x) {
+    const uint32_t x = dc % a.nx;
+    const uint32_t t = dc / a.nx;
+    const uint32_t y = t % a.ny, z = t / a.ny;
+    const uint32_t c = (z * a.ny + y) * a.pitch + x;
+    float d[Q];
+    static_for<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      d[i] = Store<S>::ld(f + (size_t)i * a.plane + c);
+    });
+    float dr, jx, jy, jz;
+    shifted_moments(d, dr, jx, jy, jz);
+    const float r = 1.0f + dr;
+    if constexpr (FORCE) {
+      jx = fmaf(-0.5f, __ldg(a.force + dc), jx);
+      jy = fmaf(-0.5f, __ldg(a.force + a.cells + dc), jy);
+      jz = fmaf(-0.5f, __ldg(a.force + 2 * (size_t)a.cells + dc), jz);
+    }
+    const float rinv = __frcp_rn(r);
+    if (rho) rho[dc] = r;
+    if (u) {
+      u[dc] = jx * rinv;
+      u[a.cells + dc] = jy * rinv;
+      u[2 * (size_t)a.cells + dc] = jz * rinv;
+    }
+    acc += (double)dr;
+    bad |= !isfinite(r);
+  }
+  if (!partials) return;
+  // block reduction of acc (warp shuffles, then one warp over the warps)
+  __shared__ double red[kReduceThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = acc;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, kErrNonFinite);
+  if (wid == 0) {
+    acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) partials[blockIdx.x] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+    k_finalize(const double *__restrict__ partials, int n, double offset,
+               double *__restrict__ out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (wid == 0) {
+    acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) *out = offset + acc;
+  }
+}
+
+// ---- launchers ---------------------------------------------------------------
+
+static dim3 node_grid(const StepArgs &a, int bx, int by) {
+  return dim3((a.nx + bx - 1) / bx, (a.ny + by - 1) / by, a.nz);
+}
+
+template <int S>
+static void step_dispatch(bool moments, const StepArgs &a, dim3 g, dim3 b,
+                          cudaStream_t s) {
+  const bool walls = a.walls != 0, force = a.force != nullptr;
+#define LBM_STEP_CASE(W, F, M)                                  \
+  if (walls == W && force == F && moments == M) {               \
+    k_step<S, W, F, M><<<g, b, 0, s>>>(a);                      \
+    return;                                                     \
+  }
+  LBM_STEP_CASE(false, false, false)
+  LBM_STEP_CASE(false, false, true)
+  LBM_STEP_CASE(false, true, false)
+  LBM_STEP_CASE(false, true, true)
+  LBM_STEP_CASE(true, false, false)
+  LBM_STEP_CASE(true, false, true)
+  LBM_STEP_CASE(true, true, false)
+  LBM_STEP_CASE(true, true, true)
+#undef LBM_STEP_CASE
+}
+
+cudaError_t launch_step(int storage, bool moments, const StepArgs &a, int bx,
+                        int by, cudaStream_t s) {
+  const dim3 g = node_grid(a, bx, by), b(bx, by, 1);
+  switch (storage) {
+    case kF32: step_dispatch<0>(moments, a, g, b, s); break;
+    case kF16: step_dispatch<1>(moments, a, g, b, s); break;
+    case kBF16: step_dispatch<2>(moments, a, g, b, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(int storage, const StepArgs &a, const float *rho0,
+                        const float *u0, int bx, int by, cudaStream_t s) {
+  const dim3 g = node_grid(a, bx, by), b(bx, by, 1);
+  switch (storage) {
+    case kF32: k_init<0><<<g, b, 0, s>>>(a, rho0, u0); break;
+    case kF16: k_init<1><<<g, b, 0, s>>>(a, rho0, u0); break;
+    case kBF16: k_init<2><<<g, b, 0, s>>>(a, rho0, u0); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int S>
+static void moments_dispatch(const StepArgs &a, const void *f, float *rho,
+                             float *u, double *partials, int *err, int nb,
+                             cudaStream_t s) {
+  if (a.force)
+    k_moments<S, true><<<nb, kReduceThreads, 0, s>>>(a, f, rho, u, partials, err);
+  else
+    k_moments<S, false><<<nb, kReduceThreads, 0, s>>>(a, f, rho, u, partials, err);
+}
+
+cudaError_t launch_moments(int storage, const StepArgs &a, const void *f,
+                           float *rho, float *u, const Scratch *scr,
+                           cudaStream_t s) {
+  int nb = (int)((a.cells + kReduceThreads - 1) / kReduceThreads);
+  if (nb > kReduceBlocks) nb = kReduceBlocks;
+  if (nb < 1) nb = 1;
+  double *partials = scr ? scr->partials : nullptr;
+  int *err = scr ? scr->err : nullptr;
+  switch (storage) {
+    case kF32: moments_dispatch<0>(a, f, rho, u, partials, err, nb, s); break;
+    case kF16: moments_dispatch<1>(a, f, rho, u, partials, err, nb, s); break;
+    case kBF16: moments_dispatch<2>(a, f, rho, u, partials, err, nb, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int moments_blocks(uint32_t cells) {
+  int nb = (int)((cells + kReduceThreads - 1) / kReduceThreads);
+  if (nb > kReduceBlocks) nb = kReduceBlocks;
+  return nb < 1 ? 1 : nb;
+}
+
+cudaError_t launch_finalize_sum(const Scratch &scr, int nparts, double offset,
+                                double *out, cudaStream_t s) {
+  k_finalize<<<1, 1024, 0, s>>>(scr.partials, nparts, offset, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,48 @@
+"""Byte model of the D3Q19 step (Sec. 4.1) and roofline bookkeeping.
+
+A lattice update reads 19 distribution values and writes 19 (the stores go
+to the second copy of f): 152 bytes in FP32, 76 bytes with 16-bit storage.
+Writing rho and u adds four FP32 stores (16 bytes); reading a per-cell
+force adds three FP32 loads (12 bytes). These are ALGORITHMIC bytes: what
+the update must move if every value crosses DRAM exactly once.
+"""
+
+from __future__ import annotations
+
+Q = 19
+
+
+def bytes_per_update(elem_bytes: int = 4, moments: bool = False, force: bool = False) -> int:
+    b = 2 * Q * elem_bytes
+    if moments:
+        b += 4 * 4
+    if force:
+        b += 3 * 4
+    return b
+
+
+def adjoint_bytes_per_update(force_grad: bool = True) -> int:
+    """One reverse step of the adjoint kernel: pull f^n (19 FP32 loads),
+    read lambda^{n+1} (19), write lambda^n (19), plus read and write the
+    three force-gradient components."""
+    b = 3 * Q * 4
+    if force_grad:
+        b += 2 * 3 * 4
+    return b
+
+
+def mlups_limit(bandwidth_gbs: float, bytes_per_lu: float, gib: bool = False) -> float:
+    """Throughput bound in MLUPS at a given bandwidth. ``gib`` reads GB as
+    2^30 bytes (the reading under which Sec. 4.1's printed limits follow from
+    Sec. 2.2's measured bandwidths)."""
+    unit = 2 ** 30 if gib else 1e9
+    return bandwidth_gbs * unit / bytes_per_lu / 1e6
+
+
+def achieved_gbs(mlups: float, bytes_per_lu: float) -> float:
+    return mlups * 1e6 * bytes_per_lu / 1e9
+
+
+def reynolds(u: float, tau: float, L: float) -> float:
+    """Eq. 8 solved for Re: u = (tau - 1/2) Re / (3 L)."""
+    return 3.0 * L * u / (tau - 0.5)

@@ -1,0 +1,96 @@
+"""Host-side checks of liblbm.so that need no GPU: the library loads, exports
+every function declared in include/lbm.h, and rejects bad arguments before
+any CUDA call."""
+
+import ctypes
+
+import pytest
+
+from paper_1309_1983_gb300 import build as B
+from paper_1309_1983_gb300 import capi
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return capi.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = capi.header_symbols()
+    assert "lbm_create" in names and "lbm_step" in names and "lbm_moments" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(capi.header_symbols()) <= set(capi._SIGNATURES)
+
+
+def test_strerror_names_every_code(lib):
+    for code in range(0, -8, -1):
+        s = capi.strerror(code)
+        assert s.startswith("LBM_"), s
+    assert "unknown" in capi.strerror(-99)
+
+
+@pytest.mark.parametrize("args,code", [
+    ((0, 4, 4, 0.8, 0), capi.LBM_EINVAL),
+    ((4, -1, 4, 0.8, 0), capi.LBM_EINVAL),
+    ((4, 4, 4, 0.5, 0), capi.LBM_EINVAL),
+    ((4, 4, 4, float("nan"), 0), capi.LBM_EINVAL),
+    ((4, 4, 4, 0.8, capi.LBM_LID), capi.LBM_EINVAL),
+    ((4, 4, 4, 0.8, capi.LBM_STORE_F16 | capi.LBM_STORE_BF16), capi.LBM_EINVAL),
+    ((4, 4, 4, 0.8, 0x1000), capi.LBM_EINVAL),
+    ((2048, 2048, 1024, 0.8, 0), capi.LBM_ERANGE),
+])
+def test_create_rejects_bad_arguments(lib, args, code):
+    h = ctypes.c_void_p()
+    assert lib.lbm_create(*args, ctypes.byref(h)) == code
+    assert h.value is None
+    assert capi.last_error() != ""
+
+
+@pytest.mark.parametrize("storage,eb,align", [
+    (capi.LBM_STORE_F32, 4, 8), (capi.LBM_STORE_F16, 2, 16), (capi.LBM_STORE_BF16, 2, 16)])
+def test_layout(lib, storage, eb, align):
+    h = capi.create(37, 11, 9, 0.8, storage)
+    try:
+        L = capi.layout(h)
+        assert (L.nx, L.ny, L.nz) == (37, 11, 9)
+        assert L.pitch % align == 0 and L.pitch >= 37 and L.pitch < 37 + align
+        assert L.plane == L.pitch * 11 * 9
+        assert L.f_bytes == 19 * L.plane * eb
+        assert L.elem_bytes == eb
+        assert L.cells == 37 * 11 * 9
+        assert (L.pitch * eb) % 32 == 0
+    finally:
+        lib.lbm_destroy(h)
+
+
+def test_unbound_handle_is_reported(lib):
+    h = capi.create(8, 8, 8, 0.8, capi.LBM_CAVITY)
+    try:
+        assert lib.lbm_step(h, 1) == capi.LBM_EUNBOUND
+        assert lib.lbm_moments(h, None, None, None) == capi.LBM_EUNBOUND
+        assert lib.lbm_sync(h) == capi.LBM_EUNBOUND
+        assert lib.lbm_set_lid(h, ctypes.c_float(0.05), ctypes.c_float(0), ctypes.c_float(0)) == 0
+        assert lib.lbm_set_tau(h, ctypes.c_float(0.4)) == capi.LBM_EINVAL
+        assert lib.lbm_set_block(h, 48, 1) == capi.LBM_EINVAL
+        assert lib.lbm_set_block(h, 128, 4) == capi.LBM_EINVAL
+        assert lib.lbm_set_block(h, 64, 4) == 0
+    finally:
+        lib.lbm_destroy(h)
+
+
+def test_lid_needs_lid_flag(lib):
+    h = capi.create(8, 8, 8, 0.8, capi.LBM_WALL_Z)
+    try:
+        assert lib.lbm_set_lid(h, ctypes.c_float(0.05), ctypes.c_float(0), ctypes.c_float(0)) \
+            == capi.LBM_EINVAL
+    finally:
+        lib.lbm_destroy(h)
+
+
+def test_destroy_accepts_null(lib):
+    assert lib.lbm_destroy(None) == 0

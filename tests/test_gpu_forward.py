@@ -1,0 +1,236 @@
+"""Parity of the CUDA forward path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 storage of f_i - w_i, FP32 arithmetic):
+* element-wise f after 1-10 steps: |f_gpu - f_oracle| <= 1e-6. A stored
+  shifted value is at most ~0.05 in these cases, so one FP32 rounding costs
+  <= 3e-9; a step performs O(10) dependent roundings per value, and errors
+  compound at most linearly over 10 steps (1e-7); 1e-6 leaves a 10x margin
+  while a wrong index, sign or weight moves values by >= 1e-4.
+* rho and u after 1000 steps: the stated 1e-5 criterion, max|d rho|/rho and
+  max|d u| / max|u_ref| (field-normalised; u vanishes at points).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1309_1983_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ATOL_F = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1309_1983_gb300 import build as B
+    B.build()
+    assert torch.cuda.is_available()
+
+
+def _lat(nx, ny, nz, tau, walls=(0, 0, 0), lid=None, storage="f32", force=False):
+    from paper_1309_1983_gb300.lattice import Lattice
+    return Lattice(nx, ny, nz, tau, walls=tuple(bool(w) for w in walls), lid=lid,
+                   storage=storage, force=force)
+
+
+def _olat(nx, ny, nz, tau, walls=(0, 0, 0), lid=None):
+    return O.Lattice(nx, ny, nz, tau, walls=tuple(bool(w) for w in walls),
+                     lid=lid is not None, lid_u=tuple(lid) if lid is not None else (0, 0, 0))
+
+
+def _random_state(OL, seed, amp=0.2):
+    rho = 1.0 + W.noise(OL.shape, seed, 0.02)
+    u = W.noise((3,) + OL.shape, seed + 1, 0.05)
+    f = O.init_equilibrium(OL, rho, u)
+    return f * (1.0 + W.noise(f.shape, seed + 2, amp))
+
+
+GEOMS = {
+    "periodic": dict(walls=(0, 0, 0), lid=None),
+    "walls_x": dict(walls=(1, 0, 0), lid=None),
+    "walls_y": dict(walls=(0, 1, 0), lid=None),
+    "walls_z": dict(walls=(0, 0, 1), lid=None),
+    "cavity": dict(walls=(1, 1, 1), lid=(0.05, 0.0, 0.0)),
+    "lid_3d": dict(walls=(0, 1, 1), lid=(0.04, -0.02, 0.0)),
+}
+SHAPES = [(37, 11, 9), (64, 5, 3), (129, 3, 4), (1, 7, 6), (5, 1, 1)]
+
+
+@pytest.mark.parametrize("geom", sorted(GEOMS))
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("force", [False, True])
+def test_steps_match_oracle_elementwise(geom, shape, force):
+    nx, ny, nz = shape
+    g = GEOMS[geom]
+    tau = 0.62
+    L = _lat(nx, ny, nz, tau, g["walls"], g["lid"], force=force)
+    OL = _olat(nx, ny, nz, tau, g["walls"], g["lid"])
+    f0 = _random_state(OL, 10 + nx)
+    F = W.noise((3,) + OL.shape, 99, 2e-3) if force else None
+    if force:
+        L.force.copy_(torch.from_numpy(F).float())
+    L.set_f(f0)
+    ref = f0
+    for nsteps in (1, 9):
+        L.step(nsteps)
+        ref = O.run(OL, ref, nsteps, F)
+        got = L.get_f()
+        err = np.abs(got - ref).max()
+        assert err <= ATOL_F, (geom, shape, nsteps, err)
+
+
+def test_zero_steps_is_identity():
+    L = _lat(16, 8, 4, 0.7)
+    OL = _olat(16, 8, 4, 0.7)
+    f0 = _random_state(OL, 3)
+    L.set_f(f0)
+    before = L.get_f()
+    L.step(0)
+    np.testing.assert_array_equal(L.get_f(), before)
+
+
+def _rel_errors(rho, u, rho_ref, u_ref):
+    er = np.abs(rho - rho_ref).max() / np.abs(rho_ref).max()
+    eu = np.abs(u - u_ref).max() / np.abs(u_ref).max()
+    return er, eu
+
+
+def test_cavity_32_1000_steps():
+    """Lid-driven cavity 32^3, tau = 0.6, lid (0.05, 0, 0), f = w_i, 1000
+    steps: rho and u within 1e-5 of the oracle."""
+    n, tau, lid = 32, 0.6, (0.05, 0.0, 0.0)
+    L = _lat(n, n, n, tau, (1, 1, 1), lid)
+    L.init_equilibrium()
+    L.step(1000)
+    rho, u = L.moments()
+    OL = _olat(n, n, n, tau, (1, 1, 1), lid)
+    fr = O.run(OL, O.init_equilibrium(OL), 1000)
+    rr, ur = O.moments(OL, fr)
+    er, eu = _rel_errors(rho.double().cpu().numpy(), u.double().cpu().numpy(), rr, ur)
+    assert er <= 1e-5 and eu <= 1e-5, (er, eu)
+
+
+def test_periodic_shear_wave_64_1000_steps():
+    n, tau = 64, 0.8
+    L = _lat(n, n, n, tau)
+    u0 = W.shear_wave(n, n, n, 0.01)
+    L.init_equilibrium(u=torch.from_numpy(u0).float())
+    L.step(1000)
+    rho, u = L.moments()
+    # the flow is invariant along x and y: a 1 x 1 x n oracle column is exact
+    OL = _olat(1, 1, n, tau)
+    fr = O.run(OL, O.init_equilibrium(OL, None, W.shear_wave(1, 1, n, 0.01)), 1000)
+    rr, ur = O.moments(OL, fr)
+    rho = rho.double().cpu().numpy()
+    u = u.double().cpu().numpy()
+    er, eu = _rel_errors(rho, u, np.broadcast_to(rr, rho.shape), np.broadcast_to(ur, u.shape))
+    assert er <= 1e-5 and eu <= 1e-5, (er, eu)
+
+
+def test_random_periodic_64_1000_steps():
+    """3-D random Fourier flow on a periodic 64^3 lattice (no symmetry to
+    hide an axis mix-up), 1000 steps, against the full oracle."""
+    n, tau = 64, 0.8
+    u0 = W.fourier_modes(n, n, n, seed=1, amp=0.02)
+    L = _lat(n, n, n, tau)
+    L.init_equilibrium(u=torch.from_numpy(u0).float())
+    L.step(1000)
+    rho, u = L.moments()
+    OL = _olat(n, n, n, tau)
+    fr = O.run(OL, O.init_equilibrium(OL, None, u0), 1000)
+    rr, ur = O.moments(OL, fr)
+    er, eu = _rel_errors(rho.double().cpu().numpy(), u.double().cpu().numpy(), rr, ur)
+    assert er <= 1e-5 and eu <= 1e-5, (er, eu)
+
+
+@pytest.mark.parametrize("geom", ["periodic", "cavity"])
+def test_fused_moments_equal_moment_kernel(geom):
+    g = GEOMS[geom]
+    L = _lat(40, 24, 16, 0.7, g["walls"], g["lid"], force=True)
+    L.force.copy_(torch.from_numpy(W.noise((3, 16, 24, 40), 5, 1e-3)).float())
+    L.init_equilibrium()
+    L.step(5)
+    rho1, u1 = L.step_moments(3)
+    rho2, u2 = L.moments()
+    torch.testing.assert_close(rho1, rho2, rtol=0, atol=2e-7)
+    torch.testing.assert_close(u1, u2, rtol=0, atol=2e-7)
+
+
+def test_moments_match_oracle_and_mass():
+    OL = _olat(33, 17, 9, 0.9)
+    f0 = _random_state(OL, 21)
+    F = W.noise((3,) + OL.shape, 22, 1e-3)
+    L = _lat(33, 17, 9, 0.9, force=True)
+    L.force.copy_(torch.from_numpy(F).float())
+    L.set_f(f0)
+    rho, u, mass = L.moments(mass=True)
+    rr, ur = O.moments(OL, f0, F)
+    np.testing.assert_allclose(rho.double().cpu().numpy(), rr, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(u.double().cpu().numpy(), ur, rtol=0, atol=1e-6)
+    assert abs(mass - rr.sum()) <= 1e-9 * rr.sum()
+
+
+def test_init_equilibrium_matches_oracle():
+    OL = _olat(20, 6, 5, 0.8)
+    rho0 = 1.0 + W.noise(OL.shape, 31, 0.02)
+    u0 = W.noise((3,) + OL.shape, 32, 0.05)
+    L = _lat(20, 6, 5, 0.8)
+    L.init_equilibrium(torch.from_numpy(rho0).float(), torch.from_numpy(u0).float())
+    ref = O.init_equilibrium(OL, rho0, u0)
+    assert np.abs(L.get_f() - ref).max() <= 1e-7
+
+
+def test_step_to_matches_step():
+    L = _lat(24, 10, 6, 0.7, (1, 1, 1), (0.05, 0, 0))
+    L.init_equilibrium()
+    L.step(3)
+    cur, other = L.current_buffers()
+    out = torch.empty_like(cur)
+    L.step_to(cur, out)
+    L.step(1)
+    cur2, _ = L.current_buffers()
+    torch.cuda.synchronize()
+    assert torch.equal(out, cur2)
+
+
+def test_run_host_matches_device_path():
+    n = 24
+    u0 = torch.from_numpy(W.fourier_modes(n, n, n, seed=4, amp=0.02)).float()
+    L = _lat(n, n, n, 0.8)
+    rho_h = torch.empty((n, n, n)).pin_memory()
+    u_h = torch.empty((3, n, n, n)).pin_memory()
+    L.run_host(u0.pin_memory(), 7, rho_h, u_h)
+    L2 = _lat(n, n, n, 0.8)
+    L2.init_equilibrium(u=u0.cuda())
+    L2.step(7)
+    rho, u = L2.moments()
+    assert torch.equal(rho.cpu(), rho_h) and torch.equal(u.cpu(), u_h)
+
+
+def test_nonfinite_density_is_reported():
+    from paper_1309_1983_gb300 import capi
+    L = _lat(8, 8, 8, 0.8)
+    f = O.init_equilibrium(_olat(8, 8, 8, 0.8))
+    f[0, 3, 3, 3] = np.nan
+    L.set_f(f)
+    with pytest.raises(capi.LBMError) as e:
+        L.moments(mass=True)
+    assert e.value.code == capi.LBM_ENONFINITE
+    # the handle stays usable afterwards
+    L.init_equilibrium()
+    assert abs(L.mass() - 512) < 1e-9
+
+
+@pytest.mark.parametrize("block", [(32, 1), (32, 8), (64, 4), (128, 2), (256, 1)])
+def test_block_shapes_agree(block):
+    """Every supported block shape computes the same bits."""
+    L = _lat(70, 13, 5, 0.7, (1, 1, 1), (0.05, 0, 0))
+    L.init_equilibrium()
+    L.step(4)
+    ref = L.get_f()
+    L.set_block(*block)
+    L.init_equilibrium()
+    L.step(4)
+    np.testing.assert_array_equal(L.get_f(), ref)

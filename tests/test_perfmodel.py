@@ -1,0 +1,40 @@
+"""The benchmark's byte accounting reproduces the byte model and the
+throughput limits printed in Sec. 4.1 (tests/golden/byte_model.txt)."""
+
+import os
+
+from paper_1309_1983_gb300 import perfmodel as PM
+
+
+def _golden(golden_dir):
+    kv, rows = {}, []
+    with open(os.path.join(golden_dir, "byte_model.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            if len(parts) == 2:
+                kv[parts[0]] = int(parts[1])
+            else:
+                rows.append((parts[0], float(parts[1]), int(parts[2]), int(parts[3])))
+    return kv, rows
+
+
+def test_bytes_per_update(golden_dir):
+    kv, _ = _golden(golden_dir)
+    assert PM.bytes_per_update(4) == kv["bytes_per_lu_fp32"]
+    assert PM.bytes_per_update(4, moments=True) == kv["bytes_per_lu_fp32_moments"]
+    assert PM.bytes_per_update(2) == kv["bytes_per_lu_fp32"] // 2
+
+
+def test_printed_limits(golden_dir):
+    kv, rows = _golden(golden_dir)
+    for gpu, bw, lim, lim_m in rows:
+        assert int(PM.mlups_limit(bw, kv["bytes_per_lu_fp32"], gib=True)) == lim, gpu
+        assert int(PM.mlups_limit(bw, kv["bytes_per_lu_fp32_moments"], gib=True)) == lim_m, gpu
+
+
+def test_reynolds_eq8():
+    # Eq. 8 inverted: the 32^3 cavity at tau = 0.6 with lid 0.05 is Re = 48
+    assert abs(PM.reynolds(0.05, 0.6, 32) - 48.0) < 1e-12
