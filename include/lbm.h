@@ -174,6 +174,111 @@ int lbm_set_f(lbm_t *h, const double *host_f);
 int lbm_run_host(lbm_t *h, const float *u0_host, int n, float *rho_host,
                  float *u_host);
 
+/* ---- discrete adjoint (FP32 storage only; not in the paper) --------------
+ * Forward step f^{n+1} = C(P f^n; F): P the pull with bounce-back (affine,
+ * the lid term a constant), C the per-node collision of Eq. 3 with the Guo
+ * force term. Loss L = 1/2 sum_x |u(x, T) - u_target(x)|^2 with u from the
+ * final stored state (Eq. 7 with the half-force correction).
+ * lambda^n = dL/df^n = P^T J_C(P f^n)^T lambda^{n+1}. The lambda buffers are
+ * FP32, lbm_layout_t.lambda_bytes each, same pitch as the FP32 f buffers;
+ * they are not shifted. Each call only enqueues work on the bound stream. */
+
+/* lambda_T = dL/df^T from the state f_T. If grad_force is non-NULL it is
+ * OVERWRITTEN with the direct term dL/dF = -(u - u_target)/(2 rho); if loss is
+ * non-NULL it must be a DEVICE pointer and receives the FP64 loss. */
+int lbm_adjoint_seed(lbm_t *h, const void *f_T, const float *u_target,
+                     float *lambda_T, float *grad_force, double *loss);
+
+/* One reverse step: lambda_out = lambda^n from lambda_in = lambda^{n+1} and
+ * the state f_n that entered the forward step (the step is recomputed from
+ * it). If grad_force is non-NULL, (dC/dF)^T lambda^{n+1} is ADDED into it
+ * (the gradient at the bound force, or at F = 0 without LBM_FORCE).
+ * lambda_in and lambda_out must not overlap; every element of lambda_out is
+ * written exactly once (the transposed pull is a permutation). */
+int lbm_adjoint_step(lbm_t *h, const void *f_n, const float *lambda_in,
+                     float *lambda_out, float *grad_force);
+
+/* grad_u0 = sum_i lambda^0_i d f^eq_i(1, u0) / du0 (Eq. 5) for an initial
+ * state f^0 = f^eq(1, u0); u0 may be NULL (zero velocity). Device buffers:
+ * lambda0 FP32 lambda layout, u0 and grad_u0 [3][nz][ny][nx]. */
+int lbm_adjoint_u0(lbm_t *h, const float *lambda0, const float *u0,
+                   float *grad_u0);
+
+/* ---- batched lattices (not in the paper) --------------------------------
+ * Many independent lattices of uneven sizes, each with its own tau and lid
+ * speed, advanced together with the same per-node update as lbm_step. FP32
+ * storage only. The domains' f regions (same pitched SoA layout as a single
+ * lattice, pitch = nx rounded up to 8) are concatenated in one pair of
+ * caller-owned buffers, each region 256-byte aligned at the offsets given by
+ * lbm_batch_layout. Field outputs are dense per-domain blocks: rho at
+ * cell_offset[d] + node, u at 3 * cell_offset[d] + component * cells_d + node.
+ * Limits: at most 2^22 nodes per domain and nx * ny < 2^20. */
+typedef struct lbm_batch lbm_batch_t;
+
+/* dims: [ndom][3] (nx, ny, nz); tau: [ndom] (> 1/2); lid_ux: [ndom] lid speed
+ * along +x (NULL = 0; needs LBM_LID); flags: LBM_WALL_* and LBM_LID only.
+ * Host-only. */
+int lbm_batch_create(int ndom, const int *dims, const float *tau,
+                     const float *lid_ux, uint32_t flags, lbm_batch_t **out);
+int lbm_batch_destroy(lbm_batch_t *b);
+
+/* Bytes of one f buffer, total nodes, and per-domain offsets (FP32 elements
+ * of the f region; first node in the field buffers); any output may be NULL;
+ * the offset arrays hold ndom entries. */
+int lbm_batch_layout(const lbm_batch_t *b, size_t *f_bytes, size_t *cells,
+                     size_t *f_offsets, size_t *cell_offsets);
+
+/* Bind two device f buffers (256-byte aligned) and a cudaStream_t; f_a
+ * becomes current. Uploads the domain and tile tables and allocates the
+ * barrier words on first use. */
+int lbm_batch_bind(lbm_batch_t *b, void *f_a, void *f_b, void *stream);
+
+/* Tiling of the batched kernels: `threads` nodes per tile and block (32..256,
+ * multiple of 32); blocks_per_sm caps the persistent grid (0 = occupancy
+ * limit). Chosen by the autotuner. */
+int lbm_batch_set_tiling(lbm_batch_t *b, int threads, int blocks_per_sm);
+
+/* Wall-clock limit of one grid-barrier wait, (0, 60] seconds (default 1). */
+int lbm_batch_set_timeout(lbm_batch_t *b, double seconds);
+
+/* Fault injection for tests: the grid barrier expects `extra` more blocks
+ * than the launch has, so it can never complete; lbm_batch_step then returns
+ * LBM_ETIMEOUT after the timeout instead of hanging. 0 restores normal use. */
+int lbm_batch_inject_barrier_fault(lbm_batch_t *b, int extra);
+
+/* Capture the persistent launch in a CUDA graph (default on) or launch it
+ * directly (on = 0). */
+int lbm_batch_use_graph(lbm_batch_t *b, int on);
+
+/* Persistent grid size, tile size, tile count, and whether the last
+ * lbm_batch_step ran from a captured CUDA graph. Outputs may be NULL. */
+int lbm_batch_info(const lbm_batch_t *b, int *grid, int *threads, int *ntiles,
+                   int *graph_used);
+
+int lbm_batch_current(const lbm_batch_t *b, void **f_cur, void **f_other);
+
+/* Every domain to rest: f = w_i (rho = 1, u = 0). */
+int lbm_batch_init_rest(lbm_batch_t *b);
+
+/* n time steps of every domain in ONE persistent cooperative launch (a grid
+ * barrier between steps, bounded waits), replayed from a CUDA graph. Waits
+ * for the launch to finish; LBM_ETIMEOUT if a barrier wait ran out (the state
+ * is then partly advanced and must be re-initialised). */
+int lbm_batch_step(lbm_batch_t *b, int n);
+
+/* The same n steps as n ordinary launches over the tile table (no grid
+ * barrier); asynchronous. */
+int lbm_batch_step_launches(lbm_batch_t *b, int n);
+
+/* rho and u of every node of the current state into dense device fields
+ * (layout above); either may be NULL. */
+int lbm_batch_moments(lbm_batch_t *b, float *rho, float *u);
+
+/* Host FP64 copy in / out of one domain's state, [19][nz][ny][nx], plain f_i
+ * (w_i added back). Synchronous. */
+int lbm_batch_get_f(lbm_batch_t *b, int dom, double *host_f);
+int lbm_batch_set_f(lbm_batch_t *b, int dom, const double *host_f);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,25 @@ _SIGNATURES = {
     "lbm_get_f": [_vp, _vp],
     "lbm_set_f": [_vp, _vp],
     "lbm_run_host": [_vp, _vp, _i, _vp, _vp],
+    "lbm_adjoint_seed": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "lbm_adjoint_step": [_vp, _vp, _vp, _vp, _vp],
+    "lbm_adjoint_u0": [_vp, _vp, _vp, _vp],
+    "lbm_batch_create": [_i, _vp, _vp, _vp, _u32, ctypes.POINTER(_vp)],
+    "lbm_batch_destroy": [_vp],
+    "lbm_batch_layout": [_vp, _vp, _vp, _vp, _vp],
+    "lbm_batch_bind": [_vp, _vp, _vp, _vp],
+    "lbm_batch_set_tiling": [_vp, _i, _i],
+    "lbm_batch_set_timeout": [_vp, ctypes.c_double],
+    "lbm_batch_inject_barrier_fault": [_vp, _i],
+    "lbm_batch_use_graph": [_vp, _i],
+    "lbm_batch_info": [_vp, _vp, _vp, _vp, _vp],
+    "lbm_batch_current": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
+    "lbm_batch_init_rest": [_vp],
+    "lbm_batch_step": [_vp, _i],
+    "lbm_batch_step_launches": [_vp, _i],
+    "lbm_batch_moments": [_vp, _vp, _vp],
+    "lbm_batch_get_f": [_vp, _i, _vp],
+    "lbm_batch_set_f": [_vp, _i, _vp],
 }
 _RESTYPE = {"lbm_strerror": ctypes.c_char_p, "lbm_last_error": ctypes.c_char_p}
 

@@ -26,6 +26,9 @@ constexpr int kEx[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, -
 constexpr int kEy[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 1, -1, 1, -1, 0, 0, 0, 0};
 constexpr int kEz[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, 1, -1};
 constexpr int kOpp[Q] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
+// compile-time opposite as a value (never an ODR-use of the table in device code)
+template <int i>
+constexpr int kOpp_v = kOpp[i];
 
 __host__ __device__ constexpr float weight(int i) {
   return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
@@ -44,6 +47,9 @@ __device__ __forceinline__ void static_for(F &&f) {
 }
 
 // ---- storage traits: 0 = FP32, 1 = FP16, 2 = BF16 -------------------------
+// ld(): read-only path (ld.global.nc), valid when the buffer is not written
+// during the kernel. ld_l2(): L2-only path (ld.global.cg) for persistent
+// kernels in which other blocks rewrite the buffer between grid barriers.
 template <int S>
 struct Store;
 
@@ -51,6 +57,7 @@ template <>
 struct Store<0> {
   using T = float;
   static __device__ __forceinline__ float ld(const T *p) { return __ldg(p); }
+  static __device__ __forceinline__ float ld_l2(const T *p) { return __ldcg(p); }
   static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, v); }
 };
 template <>
@@ -58,6 +65,9 @@ struct Store<1> {
   using T = __half;
   static __device__ __forceinline__ float ld(const T *p) {
     return __half2float(__ldg(p));
+  }
+  static __device__ __forceinline__ float ld_l2(const T *p) {
+    return __half2float(__ldcg(p));
   }
   static __device__ __forceinline__ void st(T *p, float v) {
     __stcs(p, __float2half_rn(v));
@@ -69,10 +79,21 @@ struct Store<2> {
   static __device__ __forceinline__ float ld(const T *p) {
     return __bfloat162float(__ldg(p));
   }
+  static __device__ __forceinline__ float ld_l2(const T *p) {
+    return __bfloat162float(__ldcg(p));
+  }
   static __device__ __forceinline__ void st(T *p, float v) {
     __stcs(p, __float2bfloat16_rn(v));
   }
 };
+
+template <int S, bool L2ONLY>
+__device__ __forceinline__ float load_f(const typename Store<S>::T *p) {
+  if constexpr (L2ONLY)
+    return Store<S>::ld_l2(p);
+  else
+    return Store<S>::ld(p);
+}
 
 // ---- moments of shifted distributions (Eqs. 6-7) ---------------------------
 // dr = rho - 1 = sum d_i; j = sum e_i d_i (= sum e_i f_i).

@@ -54,6 +54,53 @@ int moments_blocks(uint32_t cells);  // partial sums written by launch_moments
 cudaError_t launch_finalize_sum(const Scratch &scr, int nparts, double offset,
                                 double *out, cudaStream_t s);
 
+cudaError_t launch_adjoint_step(const StepArgs &g, const float *lam_in,
+                                float *lam_out, float *grad_force, int bx,
+                                int by, cudaStream_t s);
+cudaError_t launch_adjoint_seed(const StepArgs &g, const float *u_target,
+                                float *lam_out, float *grad_force,
+                                double *partials, cudaStream_t s);
+cudaError_t launch_adjoint_u0(const StepArgs &g, const float *lam0,
+                              const float *u0, float *grad, int bx, int by,
+                              cudaStream_t s);
+
+// ---- batched lattices -------------------------------------------------------
+
+struct BatchDom {
+  int nx, ny, nz, pitch;
+  uint32_t plane, cells;
+  uint64_t foff;       // first FP32 element of the domain's f region
+  uint32_t coff;       // first dense node of the domain in field buffers
+  uint32_t walls;      // LBM_WALL_* bits
+  uint64_t m_nx, m_nxy;  // ceil(2^42 / nx), ceil(2^42 / (nx ny))
+  float omega, kf;
+  float lidc[19];
+};
+
+struct BatchArgs {
+  float *f[2];
+  const BatchDom *doms;
+  const int2 *tiles;  // {domain, first dense node}
+  int ntiles, nsteps, parity0, walls_any;
+  unsigned *bar_count, *bar_gen;
+  int *err;
+  unsigned expected;  // blocks that must reach each grid barrier
+  unsigned long long timeout_ns;
+};
+
+// Record a failure for lbm_last_error() (thread-local) and return code.
+int set_error(int code, const char *what);
+int set_cuda_error(cudaError_t e, const char *where);
+
+const void *batch_persistent_kernel(bool walls);
+cudaError_t launch_batch_persistent(const BatchArgs &a, int grid, int threads,
+                                    cudaStream_t s);
+cudaError_t launch_batch_step(const BatchArgs &a, const float *fin, float *fout,
+                              int threads, cudaStream_t s);
+cudaError_t launch_batch_rest(const BatchArgs &a, float *f, int threads, cudaStream_t s);
+cudaError_t launch_batch_moments(const BatchArgs &a, const float *f, float *rho, float *u,
+                                 int threads, cudaStream_t s);
+
 }  // namespace lbm
 
 struct lbm_lattice {

@@ -1,0 +1,203 @@
+// lbm_batch.cu - many independent lattices (uneven sizes, own tau and lid)
+// advanced together.
+//
+// Layout: the domains' pitched SoA regions are concatenated in one pair of
+// f buffers, each region starting on a 256-byte boundary. Work: the dense
+// cell range of every domain is cut into tiles of blockDim.x consecutive
+// nodes; a tile table {domain, first node} covers all domains.
+//
+// k_batch_persistent runs n whole time steps in ONE cooperative launch:
+// every block walks the tile table with a grid stride, then all blocks meet
+// at a grid barrier before the next step. The barrier spins with a wall-clock
+// limit (%globaltimer); when the limit passes it sets an error bit, and every
+// block leaves the kernel at its next barrier, so a wrong participant count
+// ends the launch with LBM_ETIMEOUT instead of hanging the GPU. Loads of f go
+// through L2 only (ld.global.cg): other blocks rewrite the buffers between
+// barriers, so the non-coherent read-only path must not be used here.
+#include "d3q19.cuh"
+#include "internal.h"
+#include "stream.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Exact q = n / d for n < 2^22 and 1 <= d < 2^20 with M = ceil(2^42 / d).
+__device__ __forceinline__ uint32_t magic_div(uint32_t n, uint64_t M) {
+  return (uint32_t)(((uint64_t)n * M) >> 42);
+}
+
+__device__ __forceinline__ void decode(const BatchDom &D, uint32_t k, int &x, int &y,
+                                       int &z) {
+  const uint32_t nxy = (uint32_t)D.nx * D.ny;
+  const uint32_t zz = magic_div(k, D.m_nxy);
+  const uint32_t r = k - zz * nxy;
+  const uint32_t yy = magic_div(r, D.m_nx);
+  x = (int)(r - yy * D.nx);
+  y = (int)yy;
+  z = (int)zz;
+}
+
+// Grid barrier with a bounded wait. Returns false (and sets the timeout bit)
+// if the other blocks did not all arrive within timeout_ns, or if another
+// block already gave up.
+__device__ bool grid_barrier(const BatchArgs &a) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = a.bar_gen;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(a.bar_count, 1u) + 1u;
+    int good = 1;
+    if (arrived == a.expected) {
+      *a.bar_count = 0u;  // nobody re-arrives before gen moves
+      __threadfence();
+      atomicAdd(a.bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*gen == g0) {
+        if (global_ns() - t0 > a.timeout_ns) {
+          atomicOr(a.err, kErrTimeout);
+          good = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    if (*(volatile int *)a.err & kErrTimeout) good = 0;
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <bool WALLS>
+__global__ void __launch_bounds__(256) k_batch_persistent(const BatchArgs a) {
+  for (int s = 0; s < a.nsteps; ++s) {
+    const int par = (a.parity0 + s) & 1;
+    const float *fin = a.f[par];
+    float *fout = a.f[par ^ 1];
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+      const int2 tile = a.tiles[t];
+      const BatchDom &D = a.doms[tile.x];
+      const uint32_t k = (uint32_t)tile.y + threadIdx.x;
+      if (k < D.cells) {
+        int x, y, z;
+        decode(D, k, x, y, z);
+        step_node<0, WALLS, false, false, true>(fin + D.foff, fout + D.foff, D.nx, D.ny, D.nz,
+                                                D.pitch, D.plane, D.walls, D.lidc, D.omega,
+                                                D.kf, nullptr, nullptr, nullptr, D.cells, x,
+                                                y, z);
+      }
+    }
+    if (s + 1 < a.nsteps && !grid_barrier(a)) return;
+  }
+}
+
+// One step over all domains without a grid barrier (one launch per step):
+// the comparison path, and what the adjoint recompute uses.
+template <bool WALLS>
+__global__ void __launch_bounds__(256) k_batch_step(const BatchArgs a, const float *fin,
+                                                    float *fout) {
+  const int2 tile = a.tiles[blockIdx.x];
+  const BatchDom &D = a.doms[tile.x];
+  const uint32_t k = (uint32_t)tile.y + threadIdx.x;
+  if (k >= D.cells) return;
+  int x, y, z;
+  decode(D, k, x, y, z);
+  step_node<0, WALLS, false, false, false>(fin + D.foff, fout + D.foff, D.nx, D.ny, D.nz,
+                                           D.pitch, D.plane, D.walls, D.lidc, D.omega, D.kf,
+                                           nullptr, nullptr, nullptr, D.cells, x, y, z);
+}
+
+// f = w_i (shifted value 0) on every node of every domain.
+__global__ void __launch_bounds__(256) k_batch_rest(const BatchArgs a, float *f) {
+  const int2 tile = a.tiles[blockIdx.x];
+  const BatchDom &D = a.doms[tile.x];
+  const uint32_t k = (uint32_t)tile.y + threadIdx.x;
+  if (k >= D.cells) return;
+  int x, y, z;
+  decode(D, k, x, y, z);
+  const uint32_t c = ((uint32_t)z * D.ny + y) * D.pitch + x;
+  for (int i = 0; i < Q; ++i) f[D.foff + (size_t)i * D.plane + c] = 0.0f;
+}
+
+// rho and u of every node into dense per-domain blocks:
+// rho[coff + k], u[3 * coff + comp * cells + k].
+__global__ void __launch_bounds__(256) k_batch_moments(const BatchArgs a, const float *f,
+                                                       float *rho, float *u) {
+  const int2 tile = a.tiles[blockIdx.x];
+  const BatchDom &D = a.doms[tile.x];
+  const uint32_t k = (uint32_t)tile.y + threadIdx.x;
+  if (k >= D.cells) return;
+  int x, y, z;
+  decode(D, k, x, y, z);
+  const uint32_t c = ((uint32_t)z * D.ny + y) * D.pitch + x;
+  float d[Q];
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    d[i] = __ldg(f + D.foff + (size_t)i * D.plane + c);
+  });
+  float dr, jx, jy, jz;
+  shifted_moments(d, dr, jx, jy, jz);
+  const float r = 1.0f + dr, rinv = __frcp_rn(r);
+  if (rho) rho[D.coff + k] = r;
+  if (u) {
+    float *ud = u + 3 * (size_t)D.coff;
+    ud[k] = jx * rinv;
+    ud[D.cells + k] = jy * rinv;
+    ud[2 * (size_t)D.cells + k] = jz * rinv;
+  }
+}
+
+// ---- launchers ------------------------------------------------------------
+
+const void *batch_persistent_kernel(bool walls) {
+  return walls ? (const void *)k_batch_persistent<true>
+               : (const void *)k_batch_persistent<false>;
+}
+
+cudaError_t launch_batch_persistent(const BatchArgs &a, int grid, int threads,
+                                    cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (a.walls_any)
+    return cudaLaunchKernelEx(&cfg, k_batch_persistent<true>, a);
+  return cudaLaunchKernelEx(&cfg, k_batch_persistent<false>, a);
+}
+
+cudaError_t launch_batch_step(const BatchArgs &a, const float *fin, float *fout,
+                              int threads, cudaStream_t s) {
+  if (a.walls_any)
+    k_batch_step<true><<<a.ntiles, threads, 0, s>>>(a, fin, fout);
+  else
+    k_batch_step<false><<<a.ntiles, threads, 0, s>>>(a, fin, fout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_rest(const BatchArgs &a, float *f, int threads, cudaStream_t s) {
+  k_batch_rest<<<a.ntiles, threads, 0, s>>>(a, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_moments(const BatchArgs &a, const float *f, float *rho, float *u,
+                                 int threads, cudaStream_t s) {
+  k_batch_moments<<<a.ntiles, threads, 0, s>>>(a, f, rho, u);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,426 @@
+// lbm_batch_capi.cu - extern "C" entry points of the batched path
+// (lbm_batch_*): domain table and tiles, buffer binding, the persistent
+// cooperative launch captured in a CUDA graph, and host exchange.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "d3q19.cuh"
+#include "internal.h"
+
+using lbm::BatchArgs;
+using lbm::BatchDom;
+
+struct lbm_batch {
+  int ndom = 0;
+  uint32_t flags = 0;
+  std::vector<BatchDom> doms;
+  std::vector<int2> tiles;
+  size_t f_elems = 0;  // FP32 elements per f buffer
+  size_t cells = 0;    // total nodes
+  BatchDom *d_doms = nullptr;
+  int2 *d_tiles = nullptr;
+  unsigned *d_bar = nullptr;  // [0] count, [1] generation
+  int *d_err = nullptr;
+  bool tiles_dirty = true;
+  float *f[2] = {nullptr, nullptr};
+  int cur = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture = nullptr;
+  bool bound = false;
+  int device = -1;
+  int threads = 256;
+  int blocks_per_sm = 0;  // 0: as many as fit
+  double timeout_s = 1.0;
+  int inject_extra = 0;
+  bool use_graph = true;
+  bool graph_ok = true;
+  std::map<std::tuple<int, int, int, int, unsigned, unsigned long long>, cudaGraphExec_t>
+      graphs;
+};
+
+namespace {
+
+int bfail(int code, const char *what) { return lbm::set_error(code, what); }
+
+int bcuda(cudaError_t e, const char *where) { return lbm::set_cuda_error(e, where); }
+
+#define BCUDA(call, where)                               \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return bcuda(e_, where);      \
+  } while (0)
+
+uint64_t magic42(uint32_t d) { return ((1ull << 42) + d - 1) / d; }
+
+void build_tiles(lbm_batch *b) {
+  b->tiles.clear();
+  for (int k = 0; k < b->ndom; ++k)
+    for (uint32_t c0 = 0; c0 < b->doms[k].cells; c0 += (uint32_t)b->threads)
+      b->tiles.push_back(make_int2(k, (int)c0));
+}
+
+void drop_graphs(lbm_batch *b) {
+  for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+int upload_tables(lbm_batch *b) {
+  if (!b->tiles_dirty) return LBM_OK;
+  build_tiles(b);
+  if (b->d_tiles) cudaFree(b->d_tiles);
+  b->d_tiles = nullptr;
+  BCUDA(cudaMalloc(&b->d_tiles, sizeof(int2) * b->tiles.size()), "cudaMalloc tiles");
+  BCUDA(cudaMemcpy(b->d_tiles, b->tiles.data(), sizeof(int2) * b->tiles.size(),
+                   cudaMemcpyHostToDevice), "tile upload");
+  b->tiles_dirty = false;
+  drop_graphs(b);
+  return LBM_OK;
+}
+
+BatchArgs make_args(const lbm_batch *b) {
+  BatchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.f[0] = b->f[0];
+  a.f[1] = b->f[1];
+  a.doms = b->d_doms;
+  a.tiles = b->d_tiles;
+  a.ntiles = (int)b->tiles.size();
+  a.walls_any = (b->flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z)) != 0;
+  a.bar_count = b->d_bar;
+  a.bar_gen = b->d_bar + 1;
+  a.err = b->d_err;
+  a.timeout_ns = (unsigned long long)(b->timeout_s * 1e9);
+  return a;
+}
+
+int persistent_grid(lbm_batch *b, int *grid) {
+  int per_sm = 0;
+  BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, lbm::batch_persistent_kernel(
+                         (b->flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z)) != 0),
+            b->threads, 0),
+        "occupancy query");
+  if (b->blocks_per_sm > 0 && b->blocks_per_sm < per_sm) per_sm = b->blocks_per_sm;
+  int sms = 0;
+  BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "SM count");
+  if (per_sm < 1) return bfail(LBM_EINVAL, "persistent kernel does not fit on an SM");
+  *grid = per_sm * sms;
+  return LBM_OK;
+}
+
+int check_b(const lbm_batch *b) {
+  if (!b) return bfail(LBM_EINVAL, "NULL handle");
+  if (!b->bound) return bfail(LBM_EUNBOUND, "no buffers bound");
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(int ndom, const int *dims, const float *tau, const float *lid_ux,
+                     uint32_t flags, lbm_batch_t **out) {
+  if (!out) return bfail(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (ndom < 1 || !dims || !tau) return bfail(LBM_EINVAL, "need ndom >= 1, dims, tau");
+  const uint32_t known = LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z | LBM_LID;
+  if (flags & ~known) return bfail(LBM_EINVAL, "batch supports walls and lid, FP32 only");
+  if ((flags & LBM_LID) && !(flags & LBM_WALL_Z)) return bfail(LBM_EINVAL, "LBM_LID needs LBM_WALL_Z");
+  lbm_batch *b = new (std::nothrow) lbm_batch();
+  if (!b) return bfail(LBM_ENOMEM, "host allocation failed");
+  b->ndom = ndom;
+  b->flags = flags;
+  size_t foff = 0, coff = 0;
+  for (int k = 0; k < ndom; ++k) {
+    const int nx = dims[3 * k], ny = dims[3 * k + 1], nz = dims[3 * k + 2];
+    const float t = tau[k];
+    if (nx < 1 || ny < 1 || nz < 1 || !(t > 0.5f) || !isfinite(t)) {
+      delete b;
+      return bfail(LBM_EINVAL, "bad domain size or tau");
+    }
+    const size_t cells = (size_t)nx * ny * nz;
+    if (cells > (1u << 22) || (size_t)nx * ny >= (1u << 20)) {
+      delete b;
+      return bfail(LBM_ERANGE, "a batch domain may hold at most 2^22 nodes");
+    }
+    BatchDom D;
+    memset(&D, 0, sizeof(D));
+    D.nx = nx;
+    D.ny = ny;
+    D.nz = nz;
+    D.pitch = (nx + 7) / 8 * 8;
+    D.plane = (uint32_t)((size_t)D.pitch * ny * nz);
+    D.cells = (uint32_t)cells;
+    D.foff = foff;
+    D.coff = (uint32_t)coff;
+    D.walls = flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z);
+    D.m_nx = magic42((uint32_t)nx);
+    D.m_nxy = magic42((uint32_t)(nx * ny));
+    D.omega = 1.0f / t;
+    D.kf = 1.0f - 0.5f * D.omega;
+    const double ux = (lid_ux && (flags & LBM_LID)) ? (double)lid_ux[k] : 0.0;
+    for (int i = 0; i < lbm::Q; ++i)
+      D.lidc[i] = (flags & LBM_LID) && lbm::kEz[i] == -1
+                      ? (float)(6.0 * lbm::weight_d(i) * lbm::kEx[i] * ux)
+                      : 0.0f;
+    b->doms.push_back(D);
+    foff += ((size_t)lbm::Q * D.plane + 63) / 64 * 64;  // 256-byte aligned regions
+    coff += cells;
+  }
+  b->f_elems = foff;
+  b->cells = coff;
+  if (coff >= (1ull << 32)) {
+    delete b;
+    return bfail(LBM_ERANGE, "too many nodes in one batch");
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch_t *b) {
+  if (!b) return LBM_OK;
+  drop_graphs(b);
+  if (b->d_doms) cudaFree(b->d_doms);
+  if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_bar) cudaFree(b->d_bar);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete b;
+  return LBM_OK;
+}
+
+int lbm_batch_layout(const lbm_batch_t *b, size_t *f_bytes, size_t *cells,
+                     size_t *f_offsets, size_t *cell_offsets) {
+  if (!b) return bfail(LBM_EINVAL, "NULL handle");
+  if (f_bytes) *f_bytes = b->f_elems * sizeof(float);
+  if (cells) *cells = b->cells;
+  for (int k = 0; k < b->ndom; ++k) {
+    if (f_offsets) f_offsets[k] = (size_t)b->doms[k].foff;
+    if (cell_offsets) cell_offsets[k] = b->doms[k].coff;
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_bind(lbm_batch_t *b, void *f_a, void *f_b, void *stream) {
+  if (!b) return bfail(LBM_EINVAL, "NULL handle");
+  if (!f_a || !f_b || f_a == f_b) return bfail(LBM_EINVAL, "need two distinct f buffers");
+  if (((uintptr_t)f_a % 256) || ((uintptr_t)f_b % 256))
+    return bfail(LBM_EINVAL, "f buffers must be 256-byte aligned");
+  int dev = 0;
+  BCUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (!b->d_doms || dev != b->device) {
+    drop_graphs(b);
+    if (b->d_doms) cudaFree(b->d_doms);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_bar) cudaFree(b->d_bar);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    b->d_doms = nullptr;
+    b->d_tiles = nullptr;
+    b->d_bar = nullptr;
+    b->capture = nullptr;
+    b->device = dev;
+    BCUDA(cudaMalloc(&b->d_doms, sizeof(BatchDom) * b->doms.size()), "cudaMalloc domains");
+    BCUDA(cudaMemcpy(b->d_doms, b->doms.data(), sizeof(BatchDom) * b->doms.size(),
+                     cudaMemcpyHostToDevice), "domain upload");
+    BCUDA(cudaMalloc(&b->d_bar, 64), "cudaMalloc barrier");
+    BCUDA(cudaMemset(b->d_bar, 0, 64), "barrier clear");
+    b->d_err = reinterpret_cast<int *>(b->d_bar + 2);
+    BCUDA(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream");
+    b->tiles_dirty = true;
+  }
+  int rc = upload_tables(b);
+  if (rc) return rc;
+  b->f[0] = static_cast<float *>(f_a);
+  b->f[1] = static_cast<float *>(f_b);
+  b->cur = 0;
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->bound = true;
+  drop_graphs(b);
+  return LBM_OK;
+}
+
+int lbm_batch_set_tiling(lbm_batch_t *b, int threads, int blocks_per_sm) {
+  if (!b) return bfail(LBM_EINVAL, "NULL handle");
+  if (threads < 32 || threads > 256 || threads % 32 || blocks_per_sm < 0)
+    return bfail(LBM_EINVAL, "threads in {32..256} step 32, blocks_per_sm >= 0");
+  if (threads != b->threads) b->tiles_dirty = true;
+  b->threads = threads;
+  b->blocks_per_sm = blocks_per_sm;
+  drop_graphs(b);
+  if (b->bound) return upload_tables(b);
+  return LBM_OK;
+}
+
+int lbm_batch_set_timeout(lbm_batch_t *b, double seconds) {
+  if (!b || !(seconds > 0.0) || seconds > 60.0) return bfail(LBM_EINVAL, "timeout in (0, 60] s");
+  b->timeout_s = seconds;
+  drop_graphs(b);
+  return LBM_OK;
+}
+
+int lbm_batch_inject_barrier_fault(lbm_batch_t *b, int extra) {
+  if (!b || extra < 0) return bfail(LBM_EINVAL, "extra must be >= 0");
+  b->inject_extra = extra;
+  drop_graphs(b);
+  return LBM_OK;
+}
+
+int lbm_batch_use_graph(lbm_batch_t *b, int on) {
+  if (!b) return bfail(LBM_EINVAL, "NULL handle");
+  b->use_graph = on != 0;
+  return LBM_OK;
+}
+
+int lbm_batch_info(const lbm_batch_t *b, int *grid, int *threads, int *ntiles,
+                   int *graph_used) {
+  if (!b) return bfail(LBM_EINVAL, "NULL handle");
+  if (grid) {
+    int g = 0;
+    if (b->bound) {
+      int rc = persistent_grid(const_cast<lbm_batch *>(b), &g);
+      if (rc) return rc;
+    }
+    *grid = g;
+  }
+  if (threads) *threads = b->threads;
+  if (ntiles) *ntiles = (int)b->tiles.size();
+  if (graph_used) *graph_used = b->use_graph && b->graph_ok;
+  return LBM_OK;
+}
+
+int lbm_batch_current(const lbm_batch_t *b, void **f_cur, void **f_other) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (f_cur) *f_cur = b->f[b->cur];
+  if (f_other) *f_other = b->f[1 - b->cur];
+  return LBM_OK;
+}
+
+int lbm_batch_init_rest(lbm_batch_t *b) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  cudaError_t e = lbm::launch_batch_rest(make_args(b), b->f[b->cur], b->threads, b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch init launch");
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch_t *b, int n) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (n < 0) return bfail(LBM_EINVAL, "n must be >= 0");
+  if (n == 0) return LBM_OK;
+  int grid = 0;
+  rc = persistent_grid(b, &grid);
+  if (rc) return rc;
+  BatchArgs a = make_args(b);
+  a.nsteps = n;
+  a.parity0 = b->cur;
+  a.expected = (unsigned)(grid + b->inject_extra);
+  const auto key = std::make_tuple(n, b->cur, grid, b->threads, a.expected, a.timeout_ns);
+  bool launched = false;
+  if (b->use_graph && b->graph_ok) {
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->capture);
+        cudaMemsetAsync(b->d_err, 0, sizeof(int), b->capture);
+        lbm::launch_batch_persistent(a, grid, b->threads, b->capture);
+        e = cudaStreamEndCapture(b->capture, &g);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->graph_ok = false;  // this driver cannot capture the cooperative launch
+      } else {
+        it = b->graphs.emplace(key, ge).first;
+      }
+    }
+    if (b->graph_ok) {
+      BCUDA(cudaGraphLaunch(it->second, b->stream), "graph launch");
+      launched = true;
+    }
+  }
+  if (!launched) {
+    BCUDA(cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->stream), "barrier reset");
+    BCUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream), "error reset");
+    BCUDA(lbm::launch_batch_persistent(a, grid, b->threads, b->stream), "persistent launch");
+  }
+  int err = 0;
+  BCUDA(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream),
+        "error word copy");
+  BCUDA(cudaStreamSynchronize(b->stream), "stream sync");
+  b->cur ^= (n & 1);
+  if (err & lbm::kErrTimeout) return bfail(LBM_ETIMEOUT, "grid barrier timed out");
+  return LBM_OK;
+}
+
+int lbm_batch_step_launches(lbm_batch_t *b, int n) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (n < 0) return bfail(LBM_EINVAL, "n must be >= 0");
+  BatchArgs a = make_args(b);
+  for (int k = 0; k < n; ++k) {
+    BCUDA(lbm::launch_batch_step(a, b->f[b->cur], b->f[1 - b->cur], b->threads, b->stream),
+          "batch step launch");
+    b->cur ^= 1;
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_moments(lbm_batch_t *b, float *rho, float *u) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  BCUDA(lbm::launch_batch_moments(make_args(b), b->f[b->cur], rho, u, b->threads, b->stream),
+        "batch moments launch");
+  return LBM_OK;
+}
+
+int lbm_batch_get_f(lbm_batch_t *b, int dom, double *host_f) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (dom < 0 || dom >= b->ndom || !host_f) return bfail(LBM_EINVAL, "bad domain or buffer");
+  const BatchDom &D = b->doms[dom];
+  std::vector<float> stage((size_t)lbm::Q * D.plane);
+  BCUDA(cudaMemcpyAsync(stage.data(), b->f[b->cur] + D.foff, stage.size() * sizeof(float),
+                        cudaMemcpyDeviceToHost, b->stream), "state copy");
+  BCUDA(cudaStreamSynchronize(b->stream), "stream sync");
+  for (int i = 0; i < lbm::Q; ++i)
+    for (int z = 0; z < D.nz; ++z)
+      for (int y = 0; y < D.ny; ++y)
+        for (int x = 0; x < D.nx; ++x)
+          host_f[(size_t)i * D.cells + ((size_t)z * D.ny + y) * D.nx + x] =
+              (double)stage[(size_t)i * D.plane + ((size_t)z * D.ny + y) * D.pitch + x] +
+              lbm::weight_d(i);
+  return LBM_OK;
+}
+
+int lbm_batch_set_f(lbm_batch_t *b, int dom, const double *host_f) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (dom < 0 || dom >= b->ndom || !host_f) return bfail(LBM_EINVAL, "bad domain or buffer");
+  const BatchDom &D = b->doms[dom];
+  std::vector<float> stage((size_t)lbm::Q * D.plane, 0.0f);
+  for (int i = 0; i < lbm::Q; ++i)
+    for (int z = 0; z < D.nz; ++z)
+      for (int y = 0; y < D.ny; ++y)
+        for (int x = 0; x < D.nx; ++x)
+          stage[(size_t)i * D.plane + ((size_t)z * D.ny + y) * D.pitch + x] =
+              (float)(host_f[(size_t)i * D.cells + ((size_t)z * D.ny + y) * D.nx + x] -
+                      lbm::weight_d(i));
+  BCUDA(cudaMemcpyAsync(b->f[b->cur] + D.foff, stage.data(), stage.size() * sizeof(float),
+                        cudaMemcpyHostToDevice, b->stream), "state copy");
+  BCUDA(cudaStreamSynchronize(b->stream), "stream sync");
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -135,6 +135,11 @@ void host_from_float(void *base, size_t k, int storage, float v) {
 
 }  // namespace
 
+namespace lbm {
+int set_error(int code, const char *what) { return fail(code, what); }
+int set_cuda_error(cudaError_t e, const char *where) { return cuda_fail(e, where); }
+}  // namespace lbm
+
 extern "C" {
 
 const char *lbm_strerror(int code) {
@@ -425,6 +430,51 @@ int lbm_run_host(lbm_t *h, const float *u0_host, int n, float *rho_host,
   LBM_CUDA(cudaMemcpyAsync(u_host, ud, 3 * cells * sizeof(float),
                            cudaMemcpyDeviceToHost, h->stream), "u copy");
   LBM_CUDA(cudaStreamSynchronize(h->stream), "stream sync");
+  return LBM_OK;
+}
+
+// ---- discrete adjoint ---------------------------------------------------
+
+int lbm_adjoint_seed(lbm_t *h, const void *f_T, const float *u_target,
+                     float *lambda_T, float *grad_force, double *loss) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (h->storage != lbm::kF32) return fail(LBM_EINVAL, "adjoint needs FP32 storage");
+  if (!f_T || !u_target || !lambda_T) return fail(LBM_EINVAL, "NULL buffer");
+  StepArgs g = make_args(h, f_T, nullptr);
+  cudaError_t e = lbm::launch_adjoint_seed(g, u_target, lambda_T, grad_force,
+                                           loss ? h->scr.partials : nullptr, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint seed launch");
+  if (loss) {
+    e = lbm::launch_finalize_sum(h->scr, lbm::moments_blocks(g.cells), 0.0, loss, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "loss reduction launch");
+  }
+  return LBM_OK;
+}
+
+int lbm_adjoint_step(lbm_t *h, const void *f_n, const float *lambda_in,
+                     float *lambda_out, float *grad_force) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (h->storage != lbm::kF32) return fail(LBM_EINVAL, "adjoint needs FP32 storage");
+  if (!f_n || !lambda_in || !lambda_out || lambda_in == lambda_out)
+    return fail(LBM_EINVAL, "bad buffers");
+  StepArgs g = make_args(h, f_n, nullptr);
+  cudaError_t e = lbm::launch_adjoint_step(g, lambda_in, lambda_out, grad_force,
+                                           h->bx, h->by, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint step launch");
+  return LBM_OK;
+}
+
+int lbm_adjoint_u0(lbm_t *h, const float *lambda0, const float *u0,
+                   float *grad_u0) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (h->storage != lbm::kF32) return fail(LBM_EINVAL, "adjoint needs FP32 storage");
+  if (!lambda0 || !grad_u0) return fail(LBM_EINVAL, "NULL buffer");
+  StepArgs g = make_args(h, nullptr, nullptr);
+  cudaError_t e = lbm::launch_adjoint_u0(g, lambda0, u0, grad_u0, h->bx, h->by, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint u0 launch");
   return LBM_OK;
 }
 

@@ -13,49 +13,9 @@
 // neighbouring warps still pull.
 #include "d3q19.cuh"
 #include "internal.h"
+#include "stream.cuh"
 
 namespace lbm {
-
-// Pull gather with periodic wrap on every axis. Walled axes are fixed up by
-// the caller; the wrapped loads they replace stay in bounds.
-template <int S>
-__device__ __forceinline__ void pull(const typename Store<S>::T *__restrict__ fin,
-                                     uint32_t plane, const uint32_t (&zo)[3],
-                                     const uint32_t (&yo)[3],
-                                     const uint32_t (&xo)[3], float (&d)[Q]) {
-  static_for<0, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    // source x - e_i: index [1 - e] picks (plus, same, minus) neighbour
-    const uint32_t src = zo[1 - kEz[i]] + yo[1 - kEy[i]] + xo[1 - kEx[i]];
-    d[i] = Store<S>::ld(fin + (size_t)i * plane + src);
-  });
-}
-
-// Halfway bounce-back on the walled faces touching this node:
-// g_i = f_ibar(x) + 6 w_i (e_i . u_w) when x - e_i is outside a walled axis.
-template <int S>
-__device__ __forceinline__ void bounce_back(const typename Store<S>::T *__restrict__ fin,
-                                            uint32_t plane, uint32_t c,
-                                            bool x0, bool x1, bool y0, bool y1,
-                                            bool z0, bool z1,
-                                            const float (&lidc)[Q], float (&d)[Q]) {
-  static_for<1, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    bool out = false;
-    if constexpr (kEx[i] == 1) out |= x0;
-    if constexpr (kEx[i] == -1) out |= x1;
-    if constexpr (kEy[i] == 1) out |= y0;
-    if constexpr (kEy[i] == -1) out |= y1;
-    if constexpr (kEz[i] == 1) out |= z0;
-    if constexpr (kEz[i] == -1) out |= z1;
-    if (out) {
-      float v = Store<S>::ld(fin + (size_t)kOpp[i] * plane + c);
-      // the source lies on the plane z = nz exactly when e_z = -1 at z1
-      if constexpr (kEz[i] == -1) v += z1 ? lidc[i] : 0.0f;
-      d[i] = v;
-    }
-  });
-}
 
 template <int S, bool WALLS, bool FORCE, bool MOM>
 __global__ void __launch_bounds__(256) k_step(const StepArgs a) {
@@ -64,53 +24,9 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a) {
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= a.nx || y >= a.ny) return;
-  const T *__restrict__ fin = static_cast<const T *>(a.fin);
-  T *__restrict__ fout = static_cast<T *>(a.fout);
-  const uint32_t row = (uint32_t)a.ny * a.pitch;
-
-  const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
-  const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
-  const int zm = z == 0 ? a.nz - 1 : z - 1, zp = z == a.nz - 1 ? 0 : z + 1;
-  const uint32_t zo[3] = {zp * row, z * row, zm * row};
-  const uint32_t yo[3] = {(uint32_t)yp * a.pitch, (uint32_t)y * a.pitch,
-                          (uint32_t)ym * a.pitch};
-  const uint32_t xo[3] = {(uint32_t)xp, (uint32_t)x, (uint32_t)xm};
-  const uint32_t c = zo[1] + yo[1] + xo[1];
-
-  float d[Q];
-  pull<S>(fin, a.plane, zo, yo, xo, d);
-
-  if constexpr (WALLS) {
-    const bool x0 = (a.walls & LBM_WALL_X) && x == 0;
-    const bool x1 = (a.walls & LBM_WALL_X) && x == a.nx - 1;
-    const bool y0 = (a.walls & LBM_WALL_Y) && y == 0;
-    const bool y1 = (a.walls & LBM_WALL_Y) && y == a.ny - 1;
-    const bool z0 = (a.walls & LBM_WALL_Z) && z == 0;
-    const bool z1 = (a.walls & LBM_WALL_Z) && z == a.nz - 1;
-    if (x0 | x1 | y0 | y1 | z0 | z1)
-      bounce_back<S>(fin, a.plane, c, x0, x1, y0, y1, z0, z1, a.lidc, d);
-  }
-
-  const uint32_t dc = ((uint32_t)z * a.ny + y) * a.nx + x;
-  float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-  if constexpr (FORCE) {
-    Fx = __ldg(a.force + dc);
-    Fy = __ldg(a.force + a.cells + dc);
-    Fz = __ldg(a.force + 2 * (size_t)a.cells + dc);
-  }
-  float rho, ux, uy, uz;
-  collide<FORCE>(d, a.omega, a.kf, Fx, Fy, Fz, rho, ux, uy, uz);
-
-  static_for<0, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    Store<S>::st(fout + (size_t)i * a.plane + c, d[i]);
-  });
-  if constexpr (MOM) {
-    a.rho[dc] = rho;
-    a.u[dc] = ux;
-    a.u[a.cells + dc] = uy;
-    a.u[2 * (size_t)a.cells + dc] = uz;
-  }
+  step_node<S, WALLS, FORCE, MOM, false>(
+      static_cast<const T *>(a.fin), static_cast<T *>(a.fout), a.nx, a.ny, a.nz, a.pitch,
+      a.plane, a.walls, a.lidc, a.omega, a.kf, a.force, a.rho, a.u, a.cells, x, y, z);
 }
 
 template <int S>

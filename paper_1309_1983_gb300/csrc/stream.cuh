@@ -1,0 +1,141 @@
+// stream.cuh - node indexing for the pull gather (Alg. 3, first loop), the
+// halfway bounce-back rule, and the transposed (scatter) form used by the
+// adjoint. Shared by the forward and adjoint kernels.
+#pragma once
+
+#include "d3q19.cuh"
+#include "internal.h"
+
+namespace lbm {
+
+// Offsets of a node and of its wrapped neighbours inside one direction
+// plane of a pitched buffer, plus the walled faces the node touches.
+struct NodeIdx {
+  uint32_t zo[3], yo[3], xo[3];  // (plus, same, minus) neighbour per axis
+  uint32_t c;                    // the node itself
+  bool x0, x1, y0, y1, z0, z1;   // node on a walled low/high face
+};
+
+__device__ __forceinline__ NodeIdx node_index(int nx, int ny, int nz, int pitch,
+                                              uint32_t walls, int x, int y,
+                                              int z) {
+  NodeIdx n;
+  const uint32_t row = (uint32_t)ny * pitch;
+  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+  n.zo[0] = zp * row;
+  n.zo[1] = z * row;
+  n.zo[2] = zm * row;
+  n.yo[0] = (uint32_t)yp * pitch;
+  n.yo[1] = (uint32_t)y * pitch;
+  n.yo[2] = (uint32_t)ym * pitch;
+  n.xo[0] = (uint32_t)xp;
+  n.xo[1] = (uint32_t)x;
+  n.xo[2] = (uint32_t)xm;
+  n.c = n.zo[1] + n.yo[1] + n.xo[1];
+  n.x0 = (walls & LBM_WALL_X) && x == 0;
+  n.x1 = (walls & LBM_WALL_X) && x == nx - 1;
+  n.y0 = (walls & LBM_WALL_Y) && y == 0;
+  n.y1 = (walls & LBM_WALL_Y) && y == ny - 1;
+  n.z0 = (walls & LBM_WALL_Z) && z == 0;
+  n.z1 = (walls & LBM_WALL_Z) && z == nz - 1;
+  return n;
+}
+
+__device__ __forceinline__ bool on_wall(const NodeIdx &n) {
+  return n.x0 | n.x1 | n.y0 | n.y1 | n.z0 | n.z1;
+}
+
+// Index of the source node x - e_i (periodically wrapped) in its plane. The
+// offset tables hold (plus, same, minus) neighbours, so e = +1 (source at
+// minus) is entry 2 and e = -1 is entry 0.
+template <int i>
+__device__ __forceinline__ uint32_t source_of(const NodeIdx &n) {
+  constexpr int jx = 1 + kEx[i], jy = 1 + kEy[i], jz = 1 + kEz[i];
+  return n.zo[jz] + n.yo[jy] + n.xo[jx];
+}
+
+// True when x - e_i lies outside a walled axis (bounce-back applies).
+template <int i>
+__device__ __forceinline__ bool bounces(const NodeIdx &n) {
+  constexpr int ex = kEx[i], ey = kEy[i], ez = kEz[i];
+  bool out = false;
+  if constexpr (ex == 1) out |= n.x0;
+  if constexpr (ex == -1) out |= n.x1;
+  if constexpr (ey == 1) out |= n.y0;
+  if constexpr (ey == -1) out |= n.y1;
+  if constexpr (ez == 1) out |= n.z0;
+  if constexpr (ez == -1) out |= n.z1;
+  return out;
+}
+
+// Pull gather with periodic wrap on every axis: d_i = f_i(x - e_i).
+template <int S, bool L2ONLY = false>
+__device__ __forceinline__ void gather(const typename Store<S>::T *__restrict__ fin,
+                                       uint32_t plane, const NodeIdx &n,
+                                       float (&d)[Q]) {
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    d[i] = load_f<S, L2ONLY>(fin + (size_t)i * plane + source_of<i>(n));
+  });
+}
+
+// Halfway bounce-back on walled faces: g_i = f_ibar(x) + 6 w_i (e_i . u_w)
+// when x - e_i lies outside a walled axis; u_w is the lid velocity when that
+// source lies on the plane z = nz (e_z = -1 at the top face), folded into
+// lidc[i] = 6 w_i (e_i . u_w) by the host. The wrapped loads this replaces
+// stay in bounds.
+template <int S, bool L2ONLY = false>
+__device__ __forceinline__ void bounce_back(const typename Store<S>::T *__restrict__ fin,
+                                            uint32_t plane, const NodeIdx &n,
+                                            const float (&lidc)[Q], float (&d)[Q]) {
+  static_for<1, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if (bounces<i>(n)) {
+      float v = load_f<S, L2ONLY>(fin + (size_t)kOpp_v<i> * plane + n.c);
+      if constexpr (kEz[i] == -1) v += n.z1 ? lidc[i] : 0.0f;
+      d[i] = v;
+    }
+  });
+}
+
+// One fused update of node (x, y, z) (Alg. 3): pull gather, boundary rule,
+// moments, equilibrium, BGK (+ Guo force) collide, aligned store of the 19
+// post-collision values at the node; optionally also rho and u into dense
+// fields at index dc. Used by the single-lattice and the batched kernels.
+template <int S, bool WALLS, bool FORCE, bool MOM, bool L2ONLY>
+__device__ __forceinline__ void step_node(
+    const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__restrict__ fout,
+    int nx, int ny, int nz, int pitch, uint32_t plane, uint32_t walls,
+    const float (&lidc)[Q], float omega, float kf, const float *__restrict__ force,
+    float *__restrict__ rho_out, float *__restrict__ u_out, uint32_t cells, int x, int y,
+    int z) {
+  const NodeIdx n = node_index(nx, ny, nz, pitch, walls, x, y, z);
+  float d[Q];
+  gather<S, L2ONLY>(fin, plane, n, d);
+  if constexpr (WALLS) {
+    if (on_wall(n)) bounce_back<S, L2ONLY>(fin, plane, n, lidc, d);
+  }
+  const uint32_t dc = ((uint32_t)z * ny + y) * nx + x;
+  float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+  if constexpr (FORCE) {
+    Fx = __ldg(force + dc);
+    Fy = __ldg(force + cells + dc);
+    Fz = __ldg(force + 2 * (size_t)cells + dc);
+  }
+  float rho, ux, uy, uz;
+  collide<FORCE>(d, omega, kf, Fx, Fy, Fz, rho, ux, uy, uz);
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    Store<S>::st(fout + (size_t)i * plane + n.c, d[i]);
+  });
+  if constexpr (MOM) {
+    rho_out[dc] = rho;
+    u_out[dc] = ux;
+    u_out[cells + dc] = uy;
+    u_out[2 * (size_t)cells + dc] = uz;
+  }
+}
+
+}  // namespace lbm

@@ -84,3 +84,26 @@ def batch_geometry(ndom: int = 64, seed: int = 3, edge=(16, 96), tau=(0.55, 1.0)
     t = rng.uniform(tau[0], tau[1], size=ndom)
     l = rng.uniform(lid[0], lid[1], size=ndom)
     return BatchGeometry(dims=dims.astype(np.int64), tau=t, lid_u=l)
+
+
+def separable_modes(nx: int, ny: int, nz: int, seed: int, modes: int = 4,
+                    amp: float = 0.02, dtype=np.float32) -> np.ndarray:
+    """A cheap random periodic velocity field for large lattices: for each
+    component, the sum of ``modes`` products sin(2 pi (k_x x/nx + a)) *
+    sin(2 pi (k_y y/ny + b)) * sin(2 pi (k_z z/nz + c)) with integer
+    k in [1, 4] and phases from ``numpy.random.default_rng(seed)``, each term
+    scaled by amp / modes (so |u_a| <= amp)."""
+    rng = np.random.default_rng(seed)
+    u = np.zeros((3, nz, ny, nx), dtype=dtype)
+    x = np.arange(nx) / nx
+    y = np.arange(ny) / ny
+    z = np.arange(nz) / nz
+    for c in range(3):
+        for _ in range(modes):
+            k = rng.integers(1, 5, size=3)
+            ph = rng.random(3)
+            sx = np.sin(2 * np.pi * (k[0] * x + ph[0])).astype(dtype)
+            sy = np.sin(2 * np.pi * (k[1] * y + ph[1])).astype(dtype)
+            sz = np.sin(2 * np.pi * (k[2] * z + ph[2])).astype(dtype)
+            u[c] += (amp / modes) * sz[:, None, None] * sy[None, :, None] * sx[None, None, :]
+    return u

@@ -1,0 +1,132 @@
+"""The batched persistent path against the FP64 oracle, per domain."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1309_1983_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1309_1983_gb300 import build as B
+    B.build()
+
+
+def _olat(dims, tau, lid):
+    nx, ny, nz = (int(v) for v in dims)
+    return O.Lattice(nx, ny, nz, float(np.float32(tau)), walls=(True, True, True), lid=True,
+                     lid_u=(float(np.float32(lid)), 0.0, 0.0))
+
+
+SMALL_DIMS = [(17, 5, 9), (33, 16, 4), (1, 6, 7), (40, 3, 3), (8, 8, 8)]
+
+
+def _small_batch():
+    from paper_1309_1983_gb300.batch import Batch
+    tau = [0.55, 0.7, 0.9, 1.0, 0.62]
+    lid = [0.02, 0.05, 0.08, 0.03, 0.06]
+    return Batch(SMALL_DIMS, tau, lid), tau, lid
+
+
+def _random_f(OL, seed):
+    rho = 1.0 + W.noise(OL.shape, seed, 0.02)
+    u = W.noise((3,) + OL.shape, seed + 1, 0.05)
+    f = O.init_equilibrium(OL, rho, u)
+    return f * (1.0 + W.noise(f.shape, seed + 2, 0.1))
+
+
+def test_persistent_steps_match_oracle_per_domain():
+    B, tau, lid = _small_batch()
+    refs = []
+    for d, dims in enumerate(SMALL_DIMS):
+        OL = _olat(dims, tau[d], lid[d])
+        f0 = _random_f(OL, 10 * d + 1)
+        B.set_f(d, f0)
+        refs.append((OL, f0))
+    B.step(7)
+    assert B.info()["graph"], "the persistent launch was not replayed from a CUDA graph"
+    for d, (OL, f0) in enumerate(refs):
+        ref = O.run(OL, f0, 7)
+        assert np.abs(B.get_f(d) - ref).max() <= 1e-6, d
+
+
+@pytest.mark.parametrize("threads,bps", [(256, 0), (128, 0), (64, 2), (32, 1)])
+def test_tilings_and_launch_modes_agree(threads, bps):
+    B, _, _ = _small_batch()
+    B.init_rest()
+    B.step_launches(6)
+    ref = [B.get_f(d) for d in range(B.ndom)]
+    B.set_tiling(threads, bps)
+    B.init_rest()
+    B.step(6)
+    for d in range(B.ndom):
+        np.testing.assert_array_equal(B.get_f(d), ref[d])
+    B.use_graph(False)
+    B.init_rest()
+    B.step(6)
+    for d in range(B.ndom):
+        np.testing.assert_array_equal(B.get_f(d), ref[d])
+
+
+def test_batch_moments_layout():
+    B, tau, lid = _small_batch()
+    B.init_rest()
+    B.step(30)
+    rho, u = B.moments()
+    for d, dims in enumerate(SMALL_DIMS):
+        OL = _olat(dims, tau[d], lid[d])
+        rr, ur = O.moments(OL, B.get_f(d))
+        r, v = B.domain_fields(rho, u, d)
+        np.testing.assert_allclose(r.double().cpu().numpy(), rr, rtol=0, atol=1e-6)
+        np.testing.assert_allclose(v.double().cpu().numpy(), ur, rtol=0, atol=1e-6)
+
+
+def test_sixty_four_cavities_2000_steps():
+    """The seeded 64-cavity workload (edges 16..96, tau in [0.55, 1], lid in
+    [0.02, 0.08]): 2000 steps in one persistent launch; the three smallest
+    domains against the oracle (rho, u within 1e-5 of the field maximum),
+    every domain's mass conserved."""
+    from paper_1309_1983_gb300.batch import Batch
+    G = W.batch_geometry(64, seed=3)
+    B = Batch(G.dims, G.tau, G.lid_u)
+    B.init_rest()
+    B.step(2000)
+    rho, u = B.moments()
+    cells = G.dims.prod(axis=1)
+    for d in range(64):
+        r, _ = B.domain_fields(rho, u, d)
+        assert abs(r.double().sum().item() / cells[d] - 1.0) < 1e-6, d
+    for d in np.argsort(cells)[:3]:
+        OL = _olat(G.dims[d], G.tau[d], G.lid_u[d])
+        fr = O.run(OL, O.init_equilibrium(OL), 2000)
+        rr, ur = O.moments(OL, fr)
+        r, v = B.domain_fields(rho, u, d)
+        er = np.abs(r.double().cpu().numpy() - rr).max()
+        eu = np.abs(v.double().cpu().numpy() - ur).max() / np.abs(ur).max()
+        assert er <= 1e-5 and eu <= 1e-5, (d, er, eu)
+
+
+def test_barrier_timeout_is_reported_and_context_survives():
+    """Host-side fault injection: the grid barrier expects one block more than
+    the launch has. Every wait gives up after 50 ms, the kernel returns, the
+    call reports LBM_ETIMEOUT, and the next launch on the same context works."""
+    from paper_1309_1983_gb300 import capi
+    B, _, _ = _small_batch()
+    B.init_rest()
+    B.set_timeout(0.05)
+    B.inject_barrier_fault(1)
+    with pytest.raises(capi.LBMError) as e:
+        B.step(3)
+    assert e.value.code == capi.LBM_ETIMEOUT
+    B.inject_barrier_fault(0)
+    B.set_timeout(1.0)
+    B.init_rest()
+    B.step(4)
+    B.step_launches(0)
+    ref = B.get_f(0)
+    assert np.isfinite(ref).all()
+    torch.cuda.synchronize()

@@ -112,26 +112,54 @@ def test_cavity_32_1000_steps():
     assert er <= 1e-5 and eu <= 1e-5, (er, eu)
 
 
-def test_periodic_shear_wave_64_1000_steps():
-    n, tau = 64, 0.8
+@pytest.mark.parametrize("n", [64, 128])
+def test_periodic_shear_wave_decay_rate(n):
+    """Periodic cube, tau = 0.8, u_x = 0.01 sin(2 pi z/N) from equilibrium:
+    the amplitude sampled every 100 steps decays at nu k^2, nu = (tau-1/2)/3,
+    within 1% over 2000 steps; and after 1000 steps the field matches a
+    1 x 1 x N oracle column (the flow does not vary along x, y).
+
+    Field tolerance 1e-4 (not 1e-5): the wave decays to 0.38 of its start by
+    step 1000, and FP32 storage rounds each shifted value (~1e-3) to ~6e-11
+    every step; those roundings add up coherently over 1000 steps to
+    ~1e-5..4e-5 of the decayed field maximum (an FP32 emulation of the same
+    arithmetic gives 1.1e-5), so 1e-4 is the FP32 floor with a 2.5x margin.
+    """
+    tau = 0.8
     L = _lat(n, n, n, tau)
     u0 = W.shear_wave(n, n, n, 0.01)
     L.init_equilibrium(u=torch.from_numpy(u0).float())
-    L.step(1000)
-    rho, u = L.moments()
-    # the flow is invariant along x and y: a 1 x 1 x n oracle column is exact
+    s = torch.sin(2 * np.pi * torch.arange(n, dtype=torch.float64) / n).cuda()
+    t, A = [], []
+    for k in range(21):
+        if k == 10:
+            rho, u = L.moments()
+            rho10, u10 = rho.double().cpu().numpy(), u.double().cpu().numpy()
+        _, u = L.moments()
+        A.append(float((u[0].double().mean(dim=(1, 2)) * s).sum() * 2 / n))
+        t.append(100 * k)
+        if k < 20:
+            L.step(100)
+    rate = -np.polyfit(np.array(t), np.log(np.array(A)), 1)[0]
+    nu = (tau - 0.5) / 3.0
+    kk = 2 * np.pi / n
+    assert abs(rate / (nu * kk * kk) - 1.0) < 1e-2, rate / (nu * kk * kk) - 1.0
     OL = _olat(1, 1, n, tau)
     fr = O.run(OL, O.init_equilibrium(OL, None, W.shear_wave(1, 1, n, 0.01)), 1000)
     rr, ur = O.moments(OL, fr)
-    rho = rho.double().cpu().numpy()
-    u = u.double().cpu().numpy()
-    er, eu = _rel_errors(rho, u, np.broadcast_to(rr, rho.shape), np.broadcast_to(ur, u.shape))
-    assert er <= 1e-5 and eu <= 1e-5, (er, eu)
+    er, eu = _rel_errors(rho10, u10, np.broadcast_to(rr, rho10.shape), np.broadcast_to(ur, u10.shape))
+    assert er <= 1e-5 and eu <= 1e-4, (er, eu)
 
 
 def test_random_periodic_64_1000_steps():
     """3-D random Fourier flow on a periodic 64^3 lattice (no symmetry to
-    hide an axis mix-up), 1000 steps, against the full oracle."""
+    hide an axis mix-up), 1000 steps, against the full oracle.
+
+    Tolerance 1e-4 of the field maximum, as for the shear wave: the flow
+    decays freely, so each node's stored values change slowly and round the
+    same way step after step; FP32 storage rounding (2^-24 of ~1e-3) then
+    accumulates nearly linearly, ~1000 x 6e-11, i.e. a few 1e-5 of the
+    decayed velocity field (measured 3.8e-5). The driven cavity keeps 1e-5."""
     n, tau = 64, 0.8
     u0 = W.fourier_modes(n, n, n, seed=1, amp=0.02)
     L = _lat(n, n, n, tau)
@@ -142,7 +170,7 @@ def test_random_periodic_64_1000_steps():
     fr = O.run(OL, O.init_equilibrium(OL, None, u0), 1000)
     rr, ur = O.moments(OL, fr)
     er, eu = _rel_errors(rho.double().cpu().numpy(), u.double().cpu().numpy(), rr, ur)
-    assert er <= 1e-5 and eu <= 1e-5, (er, eu)
+    assert er <= 1e-5 and eu <= 1e-4, (er, eu)
 
 
 @pytest.mark.parametrize("geom", ["periodic", "cavity"])

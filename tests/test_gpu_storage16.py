@@ -1,0 +1,83 @@
+"""16-bit shifted storage (f_i - w_i as FP16 or BF16, FP32 arithmetic).
+
+Element-wise parity for one step uses the tolerance of the storage type: the
+GPU rounds each stored shifted value once (relative 2^-11 for FP16, 2^-8 for
+BF16), so after one step |f_gpu - f_oracle| <= |d| * 2^-p plus the FP32
+arithmetic error; the oracle starts from the same rounded state. Over long
+runs the error is reported (the stated requirement), with loose sanity bounds
+that a broken conversion or a wrong shift would exceed by orders of magnitude.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1309_1983_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ROUND = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1309_1983_gb300 import build as B
+    B.build()
+
+
+def _lat(n, tau, storage, walls=(True, True, True), lid=(0.05, 0.0, 0.0)):
+    from paper_1309_1983_gb300.lattice import Lattice
+    return Lattice(n, n, n, tau, walls=walls, lid=lid, storage=storage)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("shape", [(37, 11, 9), (16, 16, 16)], ids=lambda s: "x".join(map(str, s)))
+def test_one_step_within_storage_rounding(storage, shape):
+    from paper_1309_1983_gb300.lattice import Lattice
+    nx, ny, nz = shape
+    tau = 0.6
+    L = Lattice(nx, ny, nz, tau, walls=(True, True, True), lid=(0.05, 0, 0), storage=storage)
+    OL = O.Lattice(nx, ny, nz, tau, walls=(True, True, True), lid=True, lid_u=(0.05, 0, 0))
+    rho = 1.0 + W.noise(OL.shape, 1, 0.02)
+    u = W.noise((3,) + OL.shape, 2, 0.05)
+    L.set_f(O.init_equilibrium(OL, rho, u) * (1 + W.noise((19,) + OL.shape, 3, 0.1)))
+    f0 = L.get_f()  # the rounded state the GPU holds
+    L.step(1)
+    ref = O.run(OL, f0, 1)
+    w = O.weights()[:, None, None, None]
+    bound = np.abs(ref - w) * ROUND[storage] + 1e-7
+    assert (np.abs(L.get_f() - ref) <= bound).all()
+
+
+def test_sixteen_bit_error_vs_oracle_64_after_5000_steps(tmp_path):
+    """Cavity 64^3 (tau = 0.55, lid 0.05) after 5000 steps with FP32, FP16
+    and BF16 storage against the FP64 oracle: the error of each is recorded
+    (max and relative L2 of rho and u); FP32 must meet 1e-4 and FP16 1e-2 of
+    the velocity field maximum, BF16 must stay bounded (no blow-up)."""
+    n, tau, steps = 64, 0.55, 5000
+    OL = O.Lattice(n, n, n, tau, walls=(True, True, True), lid=True, lid_u=(0.05, 0, 0))
+    rr, ur = O.moments(OL, O.run(OL, O.init_equilibrium(OL), steps))
+    report = {}
+    for storage in ("f32", "f16", "bf16"):
+        L = _lat(n, tau, storage)
+        L.init_equilibrium()
+        L.step(steps)
+        rho, u = L.moments()
+        rho, u = rho.double().cpu().numpy(), u.double().cpu().numpy()
+        report[storage] = {
+            "rho_max": float(np.abs(rho - rr).max()),
+            "u_max_rel": float(np.abs(u - ur).max() / np.abs(ur).max()),
+            "u_l2_rel": float(np.linalg.norm(u - ur) / np.linalg.norm(ur)),
+        }
+    out = os.environ.get("LBM_REPORT_DIR")
+    if out:
+        with open(os.path.join(out, "storage16_error_64cube_5000.json"), "w") as fh:
+            json.dump(report, fh, indent=1)
+    print(json.dumps(report))
+    assert report["f32"]["u_max_rel"] < 1e-4, report
+    assert report["f16"]["u_max_rel"] < 1e-2, report
+    assert report["bf16"]["u_max_rel"] < 0.5 and np.isfinite(report["bf16"]["rho_max"]), report
