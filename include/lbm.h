@@ -155,6 +155,30 @@ int lbm_step_to(lbm_t *h, const void *f_in, void *f_out);
  * the stream, and returns LBM_ENONFINITE if any density was not finite. */
 int lbm_moments(lbm_t *h, float *rho, float *u, double *mass);
 
+/* Allocation-free variant of lbm_moments (the paper has no counterpart).
+ * For callers that cannot allocate device memory: code whose device memory
+ * is owned in full by another allocator (a framework's caching pool, an
+ * arena sized at start-up) and latency-critical loops in which cudaMalloc or
+ * cudaFree may synchronise the device. Needs no handle: f is a device
+ * distribution buffer in the library layout for (nx, ny, nz) and the storage
+ * type in `flags` (other flag bits are ignored; LBM_FORCE makes it subtract
+ * F/2 using `force`, [3][nz][ny][nx]). Writes rho [nz][ny][nx] and u
+ * [3][nz][ny][nx] (device FP32, either may be NULL) and, if mass is non-NULL,
+ * the FP64 total mass into the DEVICE double *mass; the work is enqueued on
+ * `stream` (cudaStream_t) and the call does not wait for it. It calls no
+ * cudaMalloc, cudaFree or allocating library routine: its reduction scratch is
+ * a fixed 9.75 KiB static device array per GPU, created when the library's
+ * device code is loaded on that GPU and kept until the process exits. The
+ * first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls on a device share the array: calls that overlap on the GPU
+ * (other streams or threads at the same time) race on it. Limit: nz * ny *
+ * pitch < 2^31 nodes (as for lbm_create); larger sizes return LBM_ERANGE
+ * without launching anything. */
+int lbm_moments_noalloc(const void *f, int nx, int ny, int nz, uint32_t flags,
+                        const float *force, float *rho, float *u, double *mass,
+                        void *stream);
+
 /* Synchronise the bound stream; LBM_ECUDA on a pending CUDA error. */
 int lbm_sync(lbm_t *h);
 

@@ -74,6 +74,7 @@ _SIGNATURES = {
     "lbm_step_moments": [_vp, _i, _vp, _vp],
     "lbm_step_to": [_vp, _vp, _vp],
     "lbm_moments": [_vp, _vp, _vp, _dp],
+    "lbm_moments_noalloc": [_vp, _i, _i, _i, _u32, _vp, _vp, _vp, _vp, _vp],
     "lbm_sync": [_vp],
     "lbm_get_f": [_vp, _vp],
     "lbm_set_f": [_vp, _vp],
