@@ -69,7 +69,8 @@ def measured_hbm():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_1309_1983_gb300/csrc/lbm_step.cu", "paper_1309_1983_gb300/csrc/d3q19.cuh"):
+    for rel in ("paper_1309_1983_gb300/csrc/lbm_step.cu", "paper_1309_1983_gb300/csrc/d3q19.cuh",
+                "paper_1309_1983_gb300/csrc/stream.cuh", "paper_1309_1983_gb300/csrc/internal.h"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -164,6 +165,16 @@ def cpu_baseline(n, steps):
     return n ** 3 * steps / dt / 1e6, O.max_threads(), dt
 
 
+def workload_config(n):
+    """The benchmarked workload, shared by both arms' JSON lines."""
+    cells = n ** 3
+    return {"workload": f"d3q19_bgk_periodic_{n}^3_fp32_shear_wave",
+            "nx": n, "ny": n, "nz": n, "tau": TAU, "storage": "f32 (f_i - w_i)",
+            "init": f"u_x = {AMP} sin(2 pi z / {n}), rho = 1, equilibrium",
+            "l2": f"inputs larger than L2 ({2 * 19 * 4 * cells / 1e9:.2f} GB working set)",
+            "bytes_per_update": 152}
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args):
@@ -191,8 +202,7 @@ def run_reference(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"d3q19_periodic_shear_wave_{args.n}^3", "tau": TAU,
-                   "sample_lattice": f"{n}^3", "parallelism": "host cores (OpenMP)"},
+        "config": workload_config(args.n),
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": O.max_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -238,6 +248,86 @@ def extra_workloads(torch, n, steps=100, warmup=10):
         del L
         torch.cuda.empty_cache()
     return out
+
+
+def adjoint_workload(torch, n=128, T=500, K=50, tau=0.7):
+    """Periodic 128^3, tau = 0.7, u0 and u_target random Fourier modes
+    (|k| <= 4, amplitude 0.02, seeds 1 and 2), F = 0, T = 500, checkpoints
+    every 50 steps: time of the forward (T steps) and of forward + backward."""
+    from paper_1309_1983_gb300 import workloads as W
+    from paper_1309_1983_gb300.adjoint import AdjointProblem
+    P = AdjointProblem(n, n, n, tau, T=T, K=K)
+    u0 = torch.from_numpy(W.fourier_modes(n, n, n, seed=1, amp=0.02)).float().cuda()
+    ut = torch.from_numpy(W.fourier_modes(n, n, n, seed=2, amp=0.02)).float().cuda()
+    F = torch.zeros((3, n, n, n), device="cuda")
+    P.loss_and_grad(u0, F, ut)  # warm-up: allocates the checkpoint pool
+    s = P.lat.stream
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(s)
+    P.forward(u0, F)
+    e[1].record(s)
+    e[1].synchronize()
+    e[2].record(s)
+    loss, gu0, gF = P.loss_and_grad(u0, F, ut)
+    e[3].record(s)
+    e[3].synchronize()
+    fwd = e[0].elapsed_time(e[1])
+    both = e[2].elapsed_time(e[3])
+    cells = n ** 3
+    out = {"config": f"periodic {n}^3 tau={tau} T={T} K={K}", "forward_ms": round(fwd, 2),
+           "forward_backward_ms": round(both, 2), "ratio": round(both / fwd, 3),
+           "forward_mlups": round(cells * T / (fwd / 1e3) / 1e6, 1),
+           "loss": float(loss.item()),
+           "grad_u0_norm": float(gu0.norm().item()), "grad_F_norm": float(gF.norm().item())}
+    del P
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_workload(torch, steps=2000):
+    """64 lid-driven cavities (seed 3: edges 16..96, tau in [0.55, 1], lid in
+    [0.02, 0.08]), autotuned tiling, `steps` steps in one persistent
+    graph-captured launch, against 64 separate single-lattice handles stepped
+    one launch per domain and step."""
+    from paper_1309_1983_gb300 import autotune, workloads as W
+    from paper_1309_1983_gb300.batch import Batch
+    from paper_1309_1983_gb300.lattice import Lattice
+    G = W.batch_geometry(64, seed=3)
+    B = Batch(G.dims, G.tau, G.lid_u)
+    tiling = autotune.tune_batch(B, steps=50, cache_path=None)
+    B.init_rest()
+    B.step(10)
+    t0 = time.perf_counter()
+    B.step(steps)
+    dt = time.perf_counter() - t0
+    cells = int(G.dims.prod(axis=1).sum())
+    info = B.info()
+    B.close()
+    lats = []
+    for d in range(64):
+        nx, ny, nz = (int(v) for v in G.dims[d])
+        L = Lattice(nx, ny, nz, float(G.tau[d]), walls=(True, True, True),
+                    lid=(float(G.lid_u[d]), 0.0, 0.0))
+        L.init_equilibrium()
+        lats.append(L)
+    sep_steps = 200
+    for L in lats:
+        L.step(2)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _ in range(sep_steps):
+        for L in lats:
+            L.step(1)
+    torch.cuda.synchronize()
+    dt_sep = time.perf_counter() - t1
+    for L in lats:
+        L.close()
+    torch.cuda.empty_cache()
+    return {"domains": 64, "cells": cells, "steps": steps,
+            "persistent_mlups": round(cells * steps / dt / 1e6, 1),
+            "separate_launches_mlups": round(cells * sep_steps / dt_sep / 1e6, 1),
+            "tiling": {"threads": tiling[0], "blocks_per_sm": tiling[1]},
+            "grid": info["grid"], "graph": info["graph"]}
 
 
 def run_ours(args):
@@ -320,6 +410,8 @@ def run_ours(args):
         del L, u0
         torch.cuda.empty_cache()
         extras = extra_workloads(torch, n)
+        extras["adjoint"] = adjoint_workload(torch)
+        extras["batched"] = batch_workload(torch)
 
     if rank != 0:
         if dist:
@@ -339,11 +431,8 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"d3q19_bgk_periodic_{n}^3_fp32_shear_wave",
-                   "nx": n, "ny": n, "nz": n, "tau": TAU, "storage": "f32 (f_i - w_i)",
-                   "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "l2": f"inputs larger than L2 ({2 * 19 * 4 * cells / 1e9:.2f} GB working set)",
-                   "bytes_per_update": bpl},
+        "config": workload_config(n),
+        "parallelism": "replicas" if ws > 1 else "single GPU",
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
