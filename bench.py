@@ -43,6 +43,15 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT, help="lattice edge (cube)")
     p.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
+    p.add_argument("--extras", default="all",
+                   help="comma list of secondary workloads: storage,adjoint,batched (or all)")
+    p.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                   help="storage of the main timed workload (profiling runs)")
+    p.add_argument("--geometry", default="periodic", choices=["periodic", "cavity"],
+                   help="geometry of the main timed workload (profiling runs)")
+    p.add_argument("--adj-n", type=int, default=128)
+    p.add_argument("--adj-steps", type=int, default=500)
+    p.add_argument("--batch-steps", type=int, default=2000)
     p.add_argument("--e2e-calls", type=int, default=5)
     p.add_argument("--cpu-sample-n", type=int, default=128)
     p.add_argument("--cpu-sample-steps", type=int, default=20)
@@ -157,12 +166,25 @@ def cpu_baseline(n, steps):
     import oracle as O
     from paper_1309_1983_gb300 import workloads as W
     L = O.Lattice(n, n, n, TAU)
-    f = O.init_equilibrium(L, None, W.shear_wave(n, n, n, AMP))
-    O.run(L, f, 1)  # warm the pages and the thread pool
+    f = O.to_aos(O.init_equilibrium(L, None, W.shear_wave(n, n, n, AMP)))
+    f = O.run_aos(L, f, 1)  # warm the pages and the thread pool
     t0 = time.perf_counter()
-    O.run(L, f, steps)
+    O.run_aos(L, f, steps)
     dt = time.perf_counter() - t0
     return n ** 3 * steps / dt / 1e6, O.max_threads(), dt
+
+
+def aggregate_replicas(ms, cells, steps, world, dist=None, device="cpu"):
+    """Whole-job throughput of ``world`` independent replicas: every rank
+    updated ``cells`` nodes ``steps`` times; the job took as long as the
+    slowest rank (max over ranks of the timed region, in ms). Returns
+    (max ms, MLUPS over all ranks)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * cells * steps / (ms_max / 1e3) / 1e6
 
 
 def workload_config(n):
@@ -185,18 +207,15 @@ def run_reference(args):
     from paper_1309_1983_gb300 import workloads as W
     n = 64
     L = O.Lattice(n, n, n, TAU)
-    f = O.init_equilibrium(L, None, W.shear_wave(n, n, n, AMP))
-    for _ in range(args.warmup):
-        f = O.run(L, f, 1)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        f = O.run(L, f, 1)
-        times.append(time.perf_counter() - t0)
-    total = sum(times)
+    f = O.to_aos(O.init_equilibrium(L, None, W.shear_wave(n, n, n, AMP)))
+    f = O.run_aos(L, f, max(args.warmup, 1))
+    t0 = time.perf_counter()
+    O.run_aos(L, f, args.steps)  # all timed steps in one call of the oracle
+    total = time.perf_counter() - t0
     mlups = n ** 3 * args.steps / total / 1e6
-    sample = (f"FP64 oracle, one update of a periodic {n}^3 shear-wave lattice per step "
-              f"(bounded sample of the {args.n}^3 workload; same per-node arithmetic)")
+    sample = (f"FP64 oracle, one update of a periodic {n}^3 shear-wave lattice per step, "
+              f"{args.steps} steps in one oracle call (bounded sample of the {args.n}^3 "
+              f"workload; same per-node arithmetic)")
     line = {
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -294,7 +313,8 @@ def batch_workload(torch, steps=2000):
     from paper_1309_1983_gb300.lattice import Lattice
     G = W.batch_geometry(64, seed=3)
     B = Batch(G.dims, G.tau, G.lid_u)
-    tiling = autotune.tune_batch(B, steps=50, cache_path=None)
+    table = {}
+    tiling = autotune.tune_batch(B, steps=50, cache_path=None, table=table)
     B.init_rest()
     B.step(10)
     t0 = time.perf_counter()
@@ -302,6 +322,13 @@ def batch_workload(torch, steps=2000):
     dt = time.perf_counter() - t0
     cells = int(G.dims.prod(axis=1).sum())
     info = B.info()
+    # the same steps as one ordinary launch per step over the tile table
+    B.step_launches(5)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    B.step_launches(200)
+    torch.cuda.synchronize()
+    dt_launch = time.perf_counter() - t2
     B.close()
     lats = []
     for d in range(64):
@@ -322,12 +349,52 @@ def batch_workload(torch, steps=2000):
     dt_sep = time.perf_counter() - t1
     for L in lats:
         L.close()
+    del lats
     torch.cuda.empty_cache()
-    return {"domains": 64, "cells": cells, "steps": steps,
+    adj = batch_adjoint_workload(torch, G, steps)
+    return {"domains": 64, "cells": cells, "steps": steps, "forward_plus_adjoint": adj,
             "persistent_mlups": round(cells * steps / dt / 1e6, 1),
+            "tile_launch_per_step_mlups": round(cells * 200 / dt_launch / 1e6, 1),
+            "tuner_ms_per_step": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in table.items()},
             "separate_launches_mlups": round(cells * sep_steps / dt_sep / 1e6, 1),
             "tiling": {"threads": tiling[0], "blocks_per_sm": tiling[1]},
             "grid": info["grid"], "graph": info["graph"]}
+
+
+def batch_adjoint_workload(torch, G, T, K=50):
+    """Forward plus adjoint over the same 64 cavities: start at rest, T steps
+    (one launch per step, checkpoints every K), loss against a seeded target
+    velocity in every domain, gradients with respect to u0 and F (at F = 0)."""
+    from paper_1309_1983_gb300 import workloads as W
+    from paper_1309_1983_gb300.adjoint import BatchAdjointProblem
+    from paper_1309_1983_gb300.batch import Batch
+    B = Batch(G.dims, G.tau, G.lid_u)
+    P = BatchAdjointProblem(B, T, K)
+    ut = B.pack_vectors([W.separable_modes(int(d[0]), int(d[1]), int(d[2]), seed=2 + k,
+                                           amp=0.02)
+                         for k, d in enumerate(G.dims)])
+    u0 = torch.zeros_like(ut)
+    F = torch.zeros_like(ut)
+    P.loss_and_grad(u0, F, ut)  # warm-up: allocates checkpoints and segment buffers
+    s = B.stream
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(s)
+    P.forward(u0, F)
+    e[1].record(s)
+    e[1].synchronize()
+    e[2].record(s)
+    loss, gu0, gF = P.loss_and_grad(u0, F, ut)
+    e[3].record(s)
+    e[3].synchronize()
+    fwd, both = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    cells = int(G.dims.prod(axis=1).sum())
+    out = {"T": T, "K": K, "forward_ms": round(fwd, 1), "forward_backward_ms": round(both, 1),
+           "ratio": round(both / fwd, 3), "forward_mlups": round(cells * T / (fwd / 1e3) / 1e6, 1),
+           "loss": float(loss.item()), "grad_u0_norm": float(gu0.norm().item()),
+           "grad_F_norm": float(gF.norm().item())}
+    del P, B
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args):
@@ -348,9 +415,13 @@ def run_ours(args):
 
     n = args.n
     cells = n ** 3
-    L = Lattice(n, n, n, TAU)
+    if args.geometry == "cavity":
+        L = Lattice(n, n, n, 0.55, walls=(True, True, True), lid=(0.05, 0.0, 0.0),
+                    storage=args.storage)
+    else:
+        L = Lattice(n, n, n, TAU, storage=args.storage)
     u0 = torch.from_numpy(W.shear_wave(n, n, n, AMP)).float().cuda()
-    L.init_equilibrium(u=u0)
+    L.init_equilibrium(u=u0 if args.geometry == "periodic" else None)
     L.step(max(args.warmup, 3))
     torch.cuda.synchronize()
 
@@ -373,11 +444,7 @@ def run_ours(args):
         dist.barrier()
     clocks = sampler.stop() if sampler else None
 
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ws * cells * args.steps / (ms_max / 1e3) / 1e6
+    ms_max, value = aggregate_replicas(ms, cells, args.steps, ws, dist, "cuda")
     per_rank_mlups = cells * args.steps / (ms / 1e3) / 1e6
     step_ms = ms / args.steps
     mlups_each = [cells / (p / 1e3) / 1e6 for p in per]
@@ -387,10 +454,11 @@ def run_ours(args):
     mass_rel = abs(mass / cells - 1.0)
 
     # roofline of the dominant (only) kernel
-    bpl = PM.bytes_per_update(4)
+    bpl = PM.bytes_per_update(4 if args.storage == "f32" else 2)
     peak, peak_kind = measured_hbm()
     achieved = bpl * cells / (step_ms / 1e3) / 1e9
-    traffic = ncu_traffic("k_step_f32_periodic_384.txt") if n == 384 else None
+    default_run = n == 384 and args.storage == "f32" and args.geometry == "periodic"
+    traffic = ncu_traffic("k_step_f32_periodic_384.txt") if default_run else None
 
     # end to end through the C ABI on host buffers
     u0_h = torch.from_numpy(W.shear_wave(n, n, n, AMP)).float().pin_memory()
@@ -409,9 +477,15 @@ def run_ours(args):
         L.close()
         del L, u0
         torch.cuda.empty_cache()
-        extras = extra_workloads(torch, n)
-        extras["adjoint"] = adjoint_workload(torch)
-        extras["batched"] = batch_workload(torch)
+        want = set(args.extras.split(",")) if args.extras != "all" else {
+            "storage", "adjoint", "batched"}
+        extras = {}
+        if "storage" in want:
+            extras.update(extra_workloads(torch, n))
+        if "adjoint" in want:
+            extras["adjoint"] = adjoint_workload(torch, n=args.adj_n, T=args.adj_steps)
+        if "batched" in want:
+            extras["batched"] = batch_workload(torch, steps=args.batch_steps)
 
     if rank != 0:
         if dist:

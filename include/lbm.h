@@ -126,6 +126,20 @@ int lbm_set_tau(lbm_t *h, float tau);
  * default is bx = min(128, nx rounded up to 32), by = 256 / bx capped at ny. */
 int lbm_set_block(lbm_t *h, int bx, int by);
 
+/* Step kernel variant. LBM_KERNEL_NODE: one node per thread (every storage
+ * type). LBM_KERNEL_PAIR: 16-bit storage only; two x-adjacent nodes per
+ * thread with 32-bit packed loads and stores and warp shuffles for the
+ * x-shifted pulls; bit-identical results. Default: NODE (on GB300 the pair
+ * kernel's shuffles and register cost made it slower, like the shuffle
+ * propagation the paper measured on Kepler, Sec. 4.3.2). */
+#define LBM_KERNEL_NODE 0
+#define LBM_KERNEL_PAIR 1
+int lbm_set_kernel(lbm_t *h, int variant);
+
+/* Block shape of the pair kernel: bxp pairs along x (a multiple of 32) by
+ * `by` rows, bxp * by <= 256. Default: 64 x 4 (or fewer rows for small ny). */
+int lbm_set_pair_block(lbm_t *h, int bxp, int by);
+
 /* Device pointers of the current state and of the other (scratch) buffer. */
 int lbm_current(const lbm_t *h, void **f_cur, void **f_other);
 
@@ -231,12 +245,12 @@ int lbm_adjoint_u0(lbm_t *h, const float *lambda0, const float *u0,
 /* ---- batched lattices (not in the paper) --------------------------------
  * Many independent lattices of uneven sizes, each with its own tau and lid
  * speed, advanced together with the same per-node update as lbm_step. FP32
- * storage only. The domains' f regions (same pitched SoA layout as a single
- * lattice, pitch = nx rounded up to 8) are concatenated in one pair of
+ * storage only. The domains' f regions (SoA [19][nz][ny][nx], unpadded rows)
+ * are concatenated in one pair of
  * caller-owned buffers, each region 256-byte aligned at the offsets given by
  * lbm_batch_layout. Field outputs are dense per-domain blocks: rho at
  * cell_offset[d] + node, u at 3 * cell_offset[d] + component * cells_d + node.
- * Limits: at most 2^22 nodes per domain and nx * ny < 2^20. */
+ * Limits: at most 256 domains, 2^22 nodes per domain and nx * ny < 2^20. */
 typedef struct lbm_batch lbm_batch_t;
 
 /* dims: [ndom][3] (nx, ny, nz); tau: [ndom] (> 1/2); lid_ux: [ndom] lid speed
@@ -293,6 +307,26 @@ int lbm_batch_step(lbm_batch_t *b, int n);
 /* The same n steps as n ordinary launches over the tile table (no grid
  * barrier); asynchronous. */
 int lbm_batch_step_launches(lbm_batch_t *b, int n);
+
+/* Every domain to f^eq(1, u0) (Eq. 5); u0 in the dense per-domain field
+ * layout (NULL = rest). */
+int lbm_batch_init_equilibrium(lbm_batch_t *b, const float *u0);
+
+/* One step of every domain from an explicit f buffer into another (batch
+ * layout, no overlap); the bound pair is not touched. */
+int lbm_batch_step_to(lbm_batch_t *b, const void *f_in, void *f_out);
+
+/* Discrete adjoint over all domains, as lbm_adjoint_seed / _step / _u0 for a
+ * single lattice (force F = 0; the force gradient is taken at F = 0). The
+ * loss is the sum over domains of 1/2 sum_x |u - u_target|^2 (FP64, device
+ * pointer). lambda buffers have the batch f layout (FP32); u_target,
+ * grad_force, u0 and grad_u0 the dense per-domain field layout. */
+int lbm_batch_adjoint_seed(lbm_batch_t *b, const void *f_T, const float *u_target,
+                           float *lambda_T, float *grad_force, double *loss);
+int lbm_batch_adjoint_step(lbm_batch_t *b, const void *f_n, const float *lambda_in,
+                           float *lambda_out, float *grad_force);
+int lbm_batch_adjoint_u0(lbm_batch_t *b, const float *lambda0, const float *u0,
+                         float *grad_u0);
 
 /* rho and u of every node of the current state into dense device fields
  * (layout above); either may be NULL. */

@@ -25,6 +25,8 @@ from .oracle import (  # noqa: F401
     stream,
     collide,
     run,
+    run_aos,
+    to_aos,
     moments,
     adjoint_seed,
     adjoint_step,

@@ -223,6 +223,23 @@ def run(L: Lattice, f, nsteps: int, force=None) -> np.ndarray:
     return _soa(out)
 
 
+def to_aos(f):
+    """(19, nz, ny, nx) -> the oracle's native (nz, ny, nx, 19) layout."""
+    return _aos(f)
+
+
+def run_aos(L: Lattice, f_aos, nsteps: int, force=None) -> np.ndarray:
+    """``run`` on an array already in the oracle's native layout (no layout
+    changes around the C call; used to time the oracle itself)."""
+    lib = library()
+    c = L.c()
+    assert f_aos.dtype == np.float64 and f_aos.flags["C_CONTIGUOUS"]
+    out = np.empty_like(f_aos)
+    _check(lib.oracle_run(ctypes.byref(c), _dp(f_aos), _dp(_vec(force, L)), int(nsteps),
+                          _dp(out)), "run")
+    return out
+
+
 def moments(L: Lattice, f, force=None):
     """(rho, u) of a stored post-collision state."""
     lib = library()

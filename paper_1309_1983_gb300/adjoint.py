@@ -4,10 +4,11 @@ Problem: the initial state is f^0 = f^eq(1, u0) (Eq. 5), T fused steps
 follow with a per-node body force F held fixed, and the loss is
 L = 1/2 sum_x |u(x, T) - u_target(x)|^2. Gradients with respect to u0 and F
 come from the library's adjoint kernels (lbm_adjoint_seed, lbm_adjoint_step,
-lbm_adjoint_u0). The forward keeps the states f^0, f^K, f^2K, ...; the
-backward recomputes each segment of K states from its checkpoint
-(lbm_step_to) and then runs the reverse steps over it, so memory holds
-ceil(T/K) checkpoints plus K - 1 segment states.
+lbm_adjoint_u0, or their lbm_batch_* counterparts for a batch of lattices).
+The forward keeps the states f^0, f^K, f^2K, ...; the backward recomputes
+each segment of K states from its checkpoint (lbm_step_to) and then runs
+the reverse steps over it, so memory holds ceil(T/K) checkpoints plus K - 1
+segment states.
 
 Every array operation runs in the library's kernels; this module only owns
 the torch buffers and orders the calls.
@@ -27,41 +28,50 @@ def _p(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
-class AdjointProblem:
-    """Geometry, tau, horizon T and checkpoint interval K of a
-    velocity-mismatch problem (FP32 storage)."""
+class _Checkpointed:
+    """Checkpoint / recompute driver; subclasses supply the kernels."""
 
-    def __init__(self, nx, ny, nz, tau, T, K=50, walls=(False, False, False), lid=None,
-                 device="cuda"):
+    def __init__(self, T, K):
         if T < 1 or K < 1:
             raise ValueError("T and K must be >= 1")
         self.T, self.K = int(T), int(K)
-        self.lat = Lattice(nx, ny, nz, tau, walls=walls, lid=lid, storage="f32", force=True,
-                           device=device)
-        self.shape = self.lat.shape
-        self.device = self.lat.device
-        lay = self.lat.layout
-        self.f_bytes = lay.f_bytes
-        self.lam_elems = lay.lambda_bytes // 4
-        self._scratch = [self._fbuf(), self._fbuf()]
+        self._scratch = None
         self._segment = []
         self._ckpt_pool = []
 
+    # -- supplied by subclasses ------------------------------------------------
     def _fbuf(self):
-        return torch.empty(self.f_bytes, dtype=torch.uint8, device=self.device)
+        raise NotImplementedError
 
-    @property
-    def launches_forward(self):
-        return 1 + self.T
+    def _init(self, u0, F):  # returns the buffer holding f^0
+        raise NotImplementedError
 
+    def _step_to(self, fin, fout):
+        raise NotImplementedError
+
+    def _seed(self, fT, ut, lam, gF, loss):
+        raise NotImplementedError
+
+    def _adj_step(self, fn, lam_in, lam_out, gF):
+        raise NotImplementedError
+
+    def _u0grad(self, lam0, u0, gu0):
+        raise NotImplementedError
+
+    def _lam(self):
+        raise NotImplementedError
+
+    def _field(self):
+        raise NotImplementedError
+
+    # -- driver -------------------------------------------------------------------
     def forward(self, u0, F):
         """f^0 = f^eq(1, u0), then T steps keeping every K-th state.
         Returns (f_T, checkpoints); the buffers stay valid until the next
         call of forward()."""
-        L = self.lat
-        L.force.copy_(F)
-        L.init_equilibrium(u=u0)
-        f0, _ = L.current_buffers()  # init writes the current buffer in place
+        if self._scratch is None:
+            self._scratch = [self._fbuf(), self._fbuf()]
+        f0 = self._init(u0, F)
         ckpts = [f0]
         prev = f0
         for n in range(1, self.T + 1):
@@ -73,19 +83,16 @@ class AdjointProblem:
                 ckpts.append(dst)
             else:
                 dst = self._scratch[n % 2]
-            L.step_to(prev, dst)
+            self._step_to(prev, dst)
             prev = dst
         return prev, ckpts
 
     def backward(self, f_T, ckpts, u0, ut):
         """Reverse sweep: (loss, grad_u0, grad_F) as device tensors."""
-        L = self.lat
-        h = L.handle
-        lam_a = torch.empty(self.lam_elems, dtype=torch.float32, device=self.device)
-        lam_b = torch.empty_like(lam_a)
-        gF = torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device)
-        loss = torch.zeros((), dtype=torch.float64, device=self.device)
-        capi.call("lbm_adjoint_seed", h, _p(f_T), _p(ut), _p(lam_a), _p(gF), _p(loss))
+        lam_a, lam_b = self._lam(), self._lam()
+        gF = self._field()
+        loss = torch.zeros((), dtype=torch.float64, device=gF.device)
+        self._seed(f_T, ut, lam_a, gF, loss)
         need = min(self.K, self.T) - 1
         while len(self._segment) < need:
             self._segment.append(self._fbuf())
@@ -94,14 +101,13 @@ class AdjointProblem:
             stop = min(start + self.K, self.T)
             states = [ckpts[s]]
             for k in range(1, stop - start):
-                L.step_to(states[-1], self._segment[k - 1])
+                self._step_to(states[-1], self._segment[k - 1])
                 states.append(self._segment[k - 1])
             for n in range(stop - 1, start - 1, -1):
-                capi.call("lbm_adjoint_step", h, _p(states[n - start]), _p(lam_a), _p(lam_b),
-                          _p(gF))
+                self._adj_step(states[n - start], lam_a, lam_b, gF)
                 lam_a, lam_b = lam_b, lam_a
-        gu0 = torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device)
-        capi.call("lbm_adjoint_u0", h, _p(lam_a), _p(u0), _p(gu0))
+        gu0 = self._field()
+        self._u0grad(lam_a, u0, gu0)
         return loss, gu0, gF
 
     def loss_and_grad(self, u0, F, u_target):
@@ -114,11 +120,98 @@ class AdjointProblem:
     def loss(self, u0, F, u_target):
         """Forward loss only (FP64 reduction on the device)."""
         f_T, _ = self.forward(u0.detach().float().contiguous(), F.detach().float().contiguous())
-        lam = torch.empty(self.lam_elems, dtype=torch.float32, device=self.device)
-        out = torch.zeros((), dtype=torch.float64, device=self.device)
-        capi.call("lbm_adjoint_seed", self.lat.handle, _p(f_T),
-                  _p(u_target.detach().float().contiguous()), _p(lam), None, _p(out))
+        lam = self._lam()
+        out = torch.zeros((), dtype=torch.float64, device=lam.device)
+        self._seed(f_T, u_target.detach().float().contiguous(), lam, None, out)
         return out
+
+
+class AdjointProblem(_Checkpointed):
+    """Geometry, tau, horizon T and checkpoint interval K of a
+    velocity-mismatch problem on one lattice (FP32 storage)."""
+
+    def __init__(self, nx, ny, nz, tau, T, K=50, walls=(False, False, False), lid=None,
+                 device="cuda"):
+        super().__init__(T, K)
+        self.lat = Lattice(nx, ny, nz, tau, walls=walls, lid=lid, storage="f32", force=True,
+                           device=device)
+        self.shape = self.lat.shape
+        self.device = self.lat.device
+        lay = self.lat.layout
+        self.f_bytes = lay.f_bytes
+        self.lam_elems = lay.lambda_bytes // 4
+
+    @property
+    def launches_forward(self):
+        return 1 + self.T
+
+    def _fbuf(self):
+        return torch.empty(self.f_bytes, dtype=torch.uint8, device=self.device)
+
+    def _init(self, u0, F):
+        self.lat.force.copy_(F)
+        self.lat.init_equilibrium(u=u0)
+        f0, _ = self.lat.current_buffers()  # init writes the current buffer in place
+        return f0
+
+    def _step_to(self, fin, fout):
+        self.lat.step_to(fin, fout)
+
+    def _seed(self, fT, ut, lam, gF, loss):
+        capi.call("lbm_adjoint_seed", self.lat.handle, _p(fT), _p(ut), _p(lam), _p(gF),
+                  _p(loss))
+
+    def _adj_step(self, fn, lam_in, lam_out, gF):
+        capi.call("lbm_adjoint_step", self.lat.handle, _p(fn), _p(lam_in), _p(lam_out), _p(gF))
+
+    def _u0grad(self, lam0, u0, gu0):
+        capi.call("lbm_adjoint_u0", self.lat.handle, _p(lam0), _p(u0), _p(gu0))
+
+    def _lam(self):
+        return torch.empty(self.lam_elems, dtype=torch.float32, device=self.device)
+
+    def _field(self):
+        return torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device)
+
+
+class BatchAdjointProblem(_Checkpointed):
+    """The same problem for every domain of a :class:`~.batch.Batch` at once
+    (F = 0; the force gradient is taken at F = 0). Fields (u0, u_target and
+    the gradients) use the batch's dense per-domain layout, see
+    :meth:`~.batch.Batch.pack_vectors`."""
+
+    def __init__(self, batch, T, K=50):
+        super().__init__(T, K)
+        self.b = batch
+        self.device = batch.device
+
+    def _fbuf(self):
+        return torch.empty(self.b.f_bytes, dtype=torch.uint8, device=self.device)
+
+    def _init(self, u0, F):
+        capi.call("lbm_batch_init_equilibrium", self.b.handle, _p(u0))
+        f0, _ = self.b.current_buffers()
+        return f0
+
+    def _step_to(self, fin, fout):
+        capi.call("lbm_batch_step_to", self.b.handle, _p(fin), _p(fout))
+
+    def _seed(self, fT, ut, lam, gF, loss):
+        capi.call("lbm_batch_adjoint_seed", self.b.handle, _p(fT), _p(ut), _p(lam), _p(gF),
+                  _p(loss))
+
+    def _adj_step(self, fn, lam_in, lam_out, gF):
+        capi.call("lbm_batch_adjoint_step", self.b.handle, _p(fn), _p(lam_in), _p(lam_out),
+                  _p(gF))
+
+    def _u0grad(self, lam0, u0, gu0):
+        capi.call("lbm_batch_adjoint_u0", self.b.handle, _p(lam0), _p(u0), _p(gu0))
+
+    def _lam(self):
+        return torch.empty(self.b.f_bytes // 4, dtype=torch.float32, device=self.device)
+
+    def _field(self):
+        return torch.empty(3 * self.b.cells, dtype=torch.float32, device=self.device)
 
 
 class VelocityMismatch(torch.autograd.Function):
@@ -128,15 +221,14 @@ class VelocityMismatch(torch.autograd.Function):
     next forward on the same problem."""
 
     @staticmethod
-    def forward(ctx, u0, F, u_target, problem: AdjointProblem):
+    def forward(ctx, u0, F, u_target, problem):
         u0c = u0.detach().float().contiguous()
         Fc = F.detach().float().contiguous()
         utc = u_target.detach().float().contiguous()
         f_T, ckpts = problem.forward(u0c, Fc)
-        lam = torch.empty(problem.lam_elems, dtype=torch.float32, device=problem.device)
-        loss = torch.zeros((), dtype=torch.float64, device=problem.device)
-        capi.call("lbm_adjoint_seed", problem.lat.handle, _p(f_T), _p(utc), _p(lam), None,
-                  _p(loss))
+        lam = problem._lam()
+        loss = torch.zeros((), dtype=torch.float64, device=u0c.device)
+        problem._seed(f_T, utc, lam, None, loss)
         ctx.problem = problem
         ctx.state = (f_T, ckpts, u0c, utc)
         ctx.dtypes = (u0.dtype, F.dtype)

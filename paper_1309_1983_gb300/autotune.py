@@ -12,6 +12,7 @@ initialising the state you want to keep (or re-initialise afterwards).
 
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 import time
@@ -85,14 +86,16 @@ def tune_lattice(L, steps=20, cache_path=DEFAULT_CACHE, candidates=None, use_cac
 
 
 def batch_candidates():
-    return [(t, b) for t in (64, 128, 256) for b in (0, 2, 4, 8)]
+    return [(t, b) for t in (64, 128, 256) for b in (0, 2, 4, 6, 8)]
 
 
-def tune_batch(B, steps=50, cache_path=DEFAULT_CACHE, candidates=None, use_cache=True):
+def tune_batch(B, steps=50, cache_path=DEFAULT_CACHE, candidates=None, use_cache=True,
+               table=None):
     """Pick the fastest (threads, blocks_per_sm) for the persistent batched
-    kernel; returns (threads, blocks_per_sm, ms per step)."""
+    kernel; returns (threads, blocks_per_sm, ms per step). ``table``, if a
+    dict, receives every candidate's time."""
     sig = ",".join(f"{a}x{b}x{c}" for a, b, c in B.dims.tolist())
-    key = f"batch:{_gpu_name(B.device)}:{B.ndom}:{hash(sig) & 0xffffffff:08x}"
+    key = f"batch:{_gpu_name(B.device)}:{B.ndom}:{hashlib.sha256(sig.encode()).hexdigest()[:12]}"
     cache = _load(cache_path) if cache_path else {}
     if use_cache and key in cache:
         t, b = cache[key]["tiling"]
@@ -105,6 +108,8 @@ def tune_batch(B, steps=50, cache_path=DEFAULT_CACHE, candidates=None, use_cache
         t0 = time.perf_counter()
         B.step(steps)
         ms = (time.perf_counter() - t0) * 1e3 / steps
+        if table is not None:
+            table[(t, b)] = ms
         if best is None or ms < best[2]:
             best = (t, b, ms)
     B.set_tiling(best[0], best[1])

@@ -100,6 +100,38 @@ class Batch:
     def init_rest(self):
         capi.call("lbm_batch_init_rest", self._h)
 
+    def init_equilibrium(self, u0=None):
+        """f = f^eq(1, u0) in every domain; u0 in the packed field layout."""
+        capi.call("lbm_batch_init_equilibrium", self._h, _p(u0))
+        self._keep = u0
+
+    def current_buffers(self):
+        cur, other = ctypes.c_void_p(), ctypes.c_void_p()
+        capi.call("lbm_batch_current", self._h, ctypes.byref(cur), ctypes.byref(other))
+        if cur.value == self.f_a.data_ptr():
+            return self.f_a, self.f_b
+        return self.f_b, self.f_a
+
+    def pack_vectors(self, fields):
+        """Per-domain (3, nz, ny, nx) arrays -> one device tensor in the
+        packed layout u[3 * cell_offset[d] + comp * cells_d + node]."""
+        out = torch.empty(3 * self.cells, dtype=torch.float32, device=self.device)
+        for d, a in enumerate(fields):
+            c0 = int(self.cell_offsets[d])
+            t = torch.as_tensor(a, dtype=torch.float32).reshape(-1)
+            out[3 * c0:3 * c0 + t.numel()] = t.to(self.device)
+        return out
+
+    def unpack_vectors(self, t):
+        """Inverse of pack_vectors: list of (3, nz, ny, nx) host arrays."""
+        host = t.detach().double().cpu().numpy()
+        res = []
+        for d in range(self.ndom):
+            nx, ny, nz = (int(v) for v in self.dims[d])
+            c0 = int(self.cell_offsets[d])
+            res.append(host[3 * c0:3 * c0 + 3 * nx * ny * nz].reshape(3, nz, ny, nx))
+        return res
+
     def step(self, n):
         """n steps in one persistent launch (synchronises)."""
         capi.call("lbm_batch_step", self._h, int(n))

@@ -34,6 +34,8 @@ LBM_STORE_F16 = 0x10
 LBM_STORE_BF16 = 0x20
 LBM_FORCE = 0x40
 LBM_CAVITY = LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z | LBM_LID
+LBM_KERNEL_NODE = 0
+LBM_KERNEL_PAIR = 1
 
 
 class LBMError(RuntimeError):
@@ -68,6 +70,8 @@ _SIGNATURES = {
     "lbm_set_lid": [_vp, _f, _f, _f],
     "lbm_set_tau": [_vp, _f],
     "lbm_set_block": [_vp, _i, _i],
+    "lbm_set_kernel": [_vp, _i],
+    "lbm_set_pair_block": [_vp, _i, _i],
     "lbm_current": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "lbm_init_equilibrium": [_vp, _vp, _vp],
     "lbm_step": [_vp, _i],
@@ -98,6 +102,11 @@ _SIGNATURES = {
     "lbm_batch_moments": [_vp, _vp, _vp],
     "lbm_batch_get_f": [_vp, _i, _vp],
     "lbm_batch_set_f": [_vp, _i, _vp],
+    "lbm_batch_init_equilibrium": [_vp, _vp],
+    "lbm_batch_step_to": [_vp, _vp, _vp],
+    "lbm_batch_adjoint_seed": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "lbm_batch_adjoint_step": [_vp, _vp, _vp, _vp, _vp],
+    "lbm_batch_adjoint_u0": [_vp, _vp, _vp, _vp],
 }
 _RESTYPE = {"lbm_strerror": ctypes.c_char_p, "lbm_last_error": ctypes.c_char_p}
 

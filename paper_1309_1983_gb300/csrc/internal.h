@@ -42,6 +42,10 @@ enum : int { kF32 = 0, kF16 = 1, kBF16 = 2 };
 
 cudaError_t launch_step(int storage, bool moments, const StepArgs &a, int bx,
                         int by, cudaStream_t s);
+// 16-bit storage, two x-adjacent nodes per thread (bxp pairs per block row,
+// a multiple of 32).
+cudaError_t launch_step_pair16(int storage, bool moments, const StepArgs &a, int bxp, int by,
+                               cudaStream_t s);
 cudaError_t launch_init(int storage, const StepArgs &a, const float *rho0,
                         const float *u0, int bx, int by, cudaStream_t s);
 // Moments of a stored state into dense rho/u (either may be null); when
@@ -82,6 +86,7 @@ struct BatchArgs {
   const BatchDom *doms;
   const int2 *tiles;  // {domain, first dense node}
   int ntiles, nsteps, parity0, walls_any;
+  int ndom;
   unsigned *bar_count, *bar_gen;
   int *err;
   unsigned expected;  // blocks that must reach each grid barrier
@@ -93,6 +98,9 @@ int set_error(int code, const char *what);
 int set_cuda_error(cudaError_t e, const char *where);
 
 const void *batch_persistent_kernel(bool walls);
+// Dynamic shared memory of the persistent kernel (the domain table).
+size_t batch_persistent_smem(int ndom);
+constexpr int kMaxBatchDomains = 256;  // table must fit in 48 KB of smem
 cudaError_t launch_batch_persistent(const BatchArgs &a, int grid, int threads,
                                     cudaStream_t s);
 cudaError_t launch_batch_step(const BatchArgs &a, const float *fin, float *fout,
@@ -100,6 +108,16 @@ cudaError_t launch_batch_step(const BatchArgs &a, const float *fin, float *fout,
 cudaError_t launch_batch_rest(const BatchArgs &a, float *f, int threads, cudaStream_t s);
 cudaError_t launch_batch_moments(const BatchArgs &a, const float *f, float *rho, float *u,
                                  int threads, cudaStream_t s);
+
+cudaError_t launch_batch_init_eq(const BatchArgs &a, float *f, const float *u0, int threads,
+                                 cudaStream_t s);
+cudaError_t launch_batch_adjoint_step(const BatchArgs &a, const float *fn, const float *lam_in,
+                                      float *lam_out, float *gF, int threads, cudaStream_t s);
+cudaError_t launch_batch_adjoint_seed(const BatchArgs &a, const float *fT, const float *ut,
+                                      float *lam, float *gF, double *partials, int threads,
+                                      cudaStream_t s);
+cudaError_t launch_batch_adjoint_u0(const BatchArgs &a, const float *lam0, const float *u0,
+                                    float *grad, int threads, cudaStream_t s);
 
 }  // namespace lbm
 
@@ -117,6 +135,8 @@ struct lbm_lattice {
   cudaStream_t stream;
   bool bound;
   int bx, by;
+  int kernel;    // LBM_KERNEL_NODE or LBM_KERNEL_PAIR (16-bit storage)
+  int pbx, pby;  // block shape of the pair kernel (pairs along x, rows)
   int device;
   lbm::Scratch scr;
 };

@@ -1,67 +1,9 @@
-// lbm_adjoint.cu - discrete adjoint of the fused step (the exact transpose
-// of the forward map; the paper has no adjoint).
-//
-// Forward step: f^{n+1} = C(P f^n; F), P = pull with bounce-back (affine; the
-// lid term is a constant), C = per-node BGK collision with Guo forcing.
-// Reverse step: lambda^n = P^T J_C(P f^n)^T lambda^{n+1}.
-//
-// Per node, with g = P f^n, rho = sum g, m = sum e g + F/2, u = m / rho and
-// the weighted moments of lambda = lambda^{n+1}(x)
-//   L0 = sum w_i lambda_i,  L1 = sum w_i lambda_i e_i,
-//   L2 = sum w_i lambda_i e_i e_i^T,
-// the collision Jacobian transpose is a rank-4 update of (1 - omega) I:
-//   mu_j = (1 - omega) lambda_j + A + B . e_j,
-//   a    = L0 + 3 u.L1 + 4.5 u.L2.u - 1.5 |u|^2 L0      (= sum lambda f^eq / rho)
-//   b    = omega rho (3 L1 + 9 L2 u - 3 u L0) + kf (9 L2 F - 3 F L0)
-//   A    = omega a - b.u / rho,  B = b / rho,  kf = 1 - omega/2,
-// and the force cotangent gains kf (3 L1 - 3 u L0 + 9 L2 u) + b / (2 rho).
-// P^T is a scatter: mu_i(x) goes to lambda^n_i(x - e_i), or to
-// lambda^n_ibar(x) when x - e_i lies outside a walled axis. Every element of
-// lambda^n receives exactly one contribution, so the scatter is a
-// permutation and needs no atomics.
-#include "d3q19.cuh"
-#include "internal.h"
-#include "stream.cuh"
+// lbm_adjoint.cu - kernels of the discrete adjoint for a single lattice
+// (per-node mathematics in adjoint.cuh): reverse step, loss seed, and the
+// gradient with respect to the initial velocity.
+#include "adjoint.cuh"
 
 namespace lbm {
-
-struct LamMoments {
-  float L0;
-  float L1[3];
-  float L2[6];  // xx, yy, zz, xy, xz, yz
-};
-
-__device__ __forceinline__ LamMoments lambda_moments(const float (&l)[Q]) {
-  LamMoments m;
-  m.L0 = weight(0) * l[0];
-  m.L1[0] = m.L1[1] = m.L1[2] = 0.0f;
-  for (int k = 0; k < 6; ++k) m.L2[k] = 0.0f;
-  static_for<0, 9>([&](auto P) {
-    constexpr int i = 2 * decltype(P)::value + 1;
-    constexpr float w = weight(i);
-    constexpr int ex = kEx[i], ey = kEy[i], ez = kEz[i];
-    const float s = w * (l[i] + l[i + 1]);  // even part (e e^T, 1)
-    const float t = w * (l[i] - l[i + 1]);  // odd part (e)
-    m.L0 += s;
-    if constexpr (ex != 0) m.L1[0] += ex * t;
-    if constexpr (ey != 0) m.L1[1] += ey * t;
-    if constexpr (ez != 0) m.L1[2] += ez * t;
-    if constexpr (ex != 0) m.L2[0] += s;
-    if constexpr (ey != 0) m.L2[1] += s;
-    if constexpr (ez != 0) m.L2[2] += s;
-    if constexpr (ex * ey != 0) m.L2[3] += (ex * ey) * s;
-    if constexpr (ex * ez != 0) m.L2[4] += (ex * ez) * s;
-    if constexpr (ey * ez != 0) m.L2[5] += (ey * ez) * s;
-  });
-  return m;
-}
-
-__device__ __forceinline__ void mat_vec(const float (&L2)[6], float vx, float vy,
-                                        float vz, float &ox, float &oy, float &oz) {
-  ox = fmaf(L2[0], vx, fmaf(L2[3], vy, L2[4] * vz));
-  oy = fmaf(L2[3], vx, fmaf(L2[1], vy, L2[5] * vz));
-  oz = fmaf(L2[4], vx, fmaf(L2[5], vy, L2[2] * vz));
-}
 
 struct AdjArgs {
   StepArgs g;             // geometry, tau, walls, lid terms, force (fin = f_n)
@@ -72,90 +14,27 @@ struct AdjArgs {
   double *partials;       // seed only: per-block FP64 loss partials
 };
 
+// Minimum resident 256-thread blocks per SM for the adjoint step: 3 caps it
+// at 80 registers, which measured 7% faster than the unconstrained 102 (more
+// resident warps for the three 76 B/node streams), while 4 (64 registers)
+// spills.
+#ifndef LBM_ADJ_MIN_BLOCKS
+#define LBM_ADJ_MIN_BLOCKS 3
+#endif
+
 template <bool FORCE, bool GRADF>
-__global__ void __launch_bounds__(256) k_adjoint_step(const AdjArgs a) {
+__global__ void __launch_bounds__(256, LBM_ADJ_MIN_BLOCKS) k_adjoint_step(const AdjArgs a) {
   const StepArgs &g = a.g;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= g.nx || y >= g.ny) return;
-  const float *__restrict__ fn = static_cast<const float *>(g.fin);
-  const NodeIdx n = node_index(g.nx, g.ny, g.nz, g.pitch, g.walls, x, y, z);
-
-  // recompute the post-streaming state g = P f^n of the forward step
-  float d[Q];
-  gather<0>(fn, g.plane, n, d);
-  if (g.walls && on_wall(n)) bounce_back<0>(fn, g.plane, n, g.lidc, d);
-
-  float lam[Q];
-  static_for<0, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    lam[i] = __ldg(a.lam_in + (size_t)i * g.plane + n.c);
-  });
-
-  const uint32_t dc = ((uint32_t)z * g.ny + y) * g.nx + x;
-  float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-  if constexpr (FORCE) {
-    Fx = __ldg(g.force + dc);
-    Fy = __ldg(g.force + g.cells + dc);
-    Fz = __ldg(g.force + 2 * (size_t)g.cells + dc);
-  }
-  float dr, jx, jy, jz;
-  shifted_moments(d, dr, jx, jy, jz);
-  const float rho = 1.0f + dr;
-  const float rinv = __frcp_rn(rho);
-  const float ux = fmaf(0.5f, Fx, jx) * rinv;
-  const float uy = fmaf(0.5f, Fy, jy) * rinv;
-  const float uz = fmaf(0.5f, Fz, jz) * rinv;
-  const float usq = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-
-  const LamMoments m = lambda_moments(lam);
-  float Lux, Luy, Luz;
-  mat_vec(m.L2, ux, uy, uz, Lux, Luy, Luz);
-  const float uL1 = fmaf(ux, m.L1[0], fmaf(uy, m.L1[1], uz * m.L1[2]));
-  const float uLu = fmaf(ux, Lux, fmaf(uy, Luy, uz * Luz));
-  const float av = fmaf(4.5f, uLu, fmaf(3.0f, uL1, m.L0 * fmaf(-1.5f, usq, 1.0f)));
-  // s = 3 L1 + 9 L2 u - 3 u L0 (the velocity derivative of sum lambda f^eq / rho)
-  const float sx = 3.0f * m.L1[0] + 9.0f * Lux - 3.0f * ux * m.L0;
-  const float sy = 3.0f * m.L1[1] + 9.0f * Luy - 3.0f * uy * m.L0;
-  const float sz = 3.0f * m.L1[2] + 9.0f * Luz - 3.0f * uz * m.L0;
-  const float om = g.omega, kf = g.kf;
-  float bx = om * rho * sx, by = om * rho * sy, bz = om * rho * sz;
-  if constexpr (FORCE) {
-    float LFx, LFy, LFz;
-    mat_vec(m.L2, Fx, Fy, Fz, LFx, LFy, LFz);
-    bx = fmaf(kf, 9.0f * LFx - 3.0f * Fx * m.L0, bx);
-    by = fmaf(kf, 9.0f * LFy - 3.0f * Fy * m.L0, by);
-    bz = fmaf(kf, 9.0f * LFz - 3.0f * Fz * m.L0, bz);
-  }
-  const float A = om * av - (bx * ux + by * uy + bz * uz) * rinv;
-  const float Bx = bx * rinv, By = by * rinv, Bz = bz * rinv;
-  const float keep = 1.0f - om;
-
-  if constexpr (GRADF) {
-    float *gF = a.grad_force;
-    gF[dc] += fmaf(kf, sx, 0.5f * Bx);
-    gF[g.cells + dc] += fmaf(kf, sy, 0.5f * By);
-    gF[2 * (size_t)g.cells + dc] += fmaf(kf, sz, 0.5f * Bz);
-  }
-
-  // mu_j = (1 - omega) lambda_j + A + B . e_j, scattered by P^T
-  float *__restrict__ out = a.lam_out;
-  const bool wall = g.walls && on_wall(n);
-  static_for<0, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    constexpr float cx = (float)kEx[i], cy = (float)kEy[i], cz = (float)kEz[i];
-    const float mu = fmaf(keep, lam[i], A + (cx * Bx + cy * By + cz * Bz));
-    if (wall && bounces<i>(n))
-      out[(size_t)kOpp_v<i> * g.plane + n.c] = mu;
-    else
-      out[(size_t)i * g.plane + source_of<i>(n)] = mu;
-  });
+  adjoint_node<FORCE, GRADF>(static_cast<const float *>(g.fin), a.lam_in, a.lam_out, g.force,
+                             a.grad_force, g.nx, g.ny, g.nz, g.pitch, g.plane, g.walls, g.lidc,
+                             g.omega, g.kf, g.cells, x, y, z);
 }
 
-// lambda^T = dL/df^T for L = 1/2 sum |u - u_t|^2, u = (sum e f - F/2)/rho:
-// lambda_j = (u - u_t) . (e_j - u) / rho; the force gains -(u - u_t)/(2 rho)
-// (written, not added); FP64 loss partials per block.
+// Seed over all nodes (grid stride), FP64 loss partials per block.
 template <bool FORCE>
 __global__ void __launch_bounds__(kReduceThreads) k_adjoint_seed(const AdjArgs a) {
   const StepArgs &g = a.g;
@@ -166,55 +45,13 @@ __global__ void __launch_bounds__(kReduceThreads) k_adjoint_seed(const AdjArgs a
     const uint32_t x = dc % g.nx;
     const uint32_t t = dc / g.nx;
     const uint32_t y = t % g.ny, z = t / g.ny;
-    const uint32_t c = (z * g.ny + y) * g.pitch + x;
-    float d[Q];
-    static_for<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      d[i] = __ldg(f + (size_t)i * g.plane + c);
-    });
-    float dr, jx, jy, jz;
-    shifted_moments(d, dr, jx, jy, jz);
-    const float rho = 1.0f + dr, rinv = __frcp_rn(rho);
-    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    if constexpr (FORCE) {
-      Fx = __ldg(g.force + dc);
-      Fy = __ldg(g.force + g.cells + dc);
-      Fz = __ldg(g.force + 2 * (size_t)g.cells + dc);
-    }
-    const float ux = fmaf(-0.5f, Fx, jx) * rinv;
-    const float uy = fmaf(-0.5f, Fy, jy) * rinv;
-    const float uz = fmaf(-0.5f, Fz, jz) * rinv;
-    const float ex = ux - __ldg(a.u_target + dc);
-    const float ey = uy - __ldg(a.u_target + g.cells + dc);
-    const float ez = uz - __ldg(a.u_target + 2 * (size_t)g.cells + dc);
-    acc += 0.5 * ((double)ex * ex + (double)ey * ey + (double)ez * ez);
-    const float du = fmaf(ex, ux, fmaf(ey, uy, ez * uz));
-    static_for<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      constexpr float cx = (float)kEx[i], cy = (float)kEy[i], cz = (float)kEz[i];
-      a.lam_out[(size_t)i * g.plane + c] = ((cx * ex + cy * ey + cz * ez) - du) * rinv;
-    });
-    if (a.grad_force) {
-      const float h = -0.5f * rinv;
-      a.grad_force[dc] = h * ex;
-      a.grad_force[g.cells + dc] = h * ey;
-      a.grad_force[2 * (size_t)g.cells + dc] = h * ez;
-    }
+    acc += seed_node<FORCE>(f, a.u_target, a.lam_out, a.grad_force, g.force, g.nx, g.ny,
+                            g.pitch, g.plane, g.cells, x, y, z);
   }
   if (!a.partials) return;
-  __shared__ double red[kReduceThreads / 32];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = acc;
-  __syncthreads();
-  if (wid == 0) {
-    acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) a.partials[blockIdx.x] = acc;
-  }
+  block_sum_to<kReduceThreads>(acc, a.partials + blockIdx.x);
 }
 
-// grad_u0 = sum_i lambda^0_i d f^eq_i(1, u0)/du0 = 3 L1 + 9 L2 u0 - 3 u0 L0.
 __global__ void __launch_bounds__(256)
     k_adjoint_u0(const StepArgs g, const float *__restrict__ lam0,
                  const float *__restrict__ u0, float *__restrict__ grad) {
@@ -222,25 +59,7 @@ __global__ void __launch_bounds__(256)
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= g.nx || y >= g.ny) return;
-  const uint32_t c = ((uint32_t)z * g.ny + y) * g.pitch + x;
-  const uint32_t dc = ((uint32_t)z * g.ny + y) * g.nx + x;
-  float lam[Q];
-  static_for<0, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    lam[i] = __ldg(lam0 + (size_t)i * g.plane + c);
-  });
-  float ux = 0.f, uy = 0.f, uz = 0.f;
-  if (u0) {
-    ux = u0[dc];
-    uy = u0[g.cells + dc];
-    uz = u0[2 * (size_t)g.cells + dc];
-  }
-  const LamMoments m = lambda_moments(lam);
-  float Lux, Luy, Luz;
-  mat_vec(m.L2, ux, uy, uz, Lux, Luy, Luz);
-  grad[dc] = 3.0f * m.L1[0] + 9.0f * Lux - 3.0f * ux * m.L0;
-  grad[g.cells + dc] = 3.0f * m.L1[1] + 9.0f * Luy - 3.0f * uy * m.L0;
-  grad[2 * (size_t)g.cells + dc] = 3.0f * m.L1[2] + 9.0f * Luz - 3.0f * uz * m.L0;
+  u0grad_node(lam0, u0, grad, g.nx, g.ny, g.pitch, g.plane, g.cells, x, y, z);
 }
 
 // ---- launchers ------------------------------------------------------------

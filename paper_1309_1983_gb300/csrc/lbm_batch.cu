@@ -14,6 +14,7 @@
 // ends the launch with LBM_ETIMEOUT instead of hanging the GPU. Loads of f go
 // through L2 only (ld.global.cg): other blocks rewrite the buffers between
 // barriers, so the non-coherent read-only path must not be used here.
+#include "adjoint.cuh"
 #include "d3q19.cuh"
 #include "internal.h"
 #include "stream.cuh"
@@ -77,15 +78,33 @@ __device__ bool grid_barrier(const BatchArgs &a) {
   return ok != 0;
 }
 
+// The domain table is copied into shared memory once per launch (it is read
+// for every tile), and the next tile's descriptor is fetched while the
+// current tile is processed, so no tile starts with a chain of dependent
+// global loads.
 template <bool WALLS>
 __global__ void __launch_bounds__(256) k_batch_persistent(const BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BatchDom *sdoms = reinterpret_cast<BatchDom *>(smem_raw);
+  {
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(a.doms);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(sdoms);
+    const int words = a.ndom * (int)(sizeof(BatchDom) / 4);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+  }
   for (int s = 0; s < a.nsteps; ++s) {
-    const int par = (a.parity0 + s) & 1;
-    const float *fin = a.f[par];
-    float *fout = a.f[par ^ 1];
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-      const int2 tile = a.tiles[t];
-      const BatchDom &D = a.doms[tile.x];
+    const bool odd = ((a.parity0 + s) & 1) != 0;
+    // selects, not a[par] indexing: a runtime index into the parameter
+    // array would move the kernel parameters to local memory
+    const float *fin = odd ? a.f[1] : a.f[0];
+    float *fout = odd ? a.f[0] : a.f[1];
+    int t = blockIdx.x;
+    int2 tile = t < a.ntiles ? a.tiles[t] : make_int2(0, 0);
+    for (; t < a.ntiles; t += gridDim.x) {
+      const int tn = t + gridDim.x;
+      const int2 next = tn < a.ntiles ? a.tiles[tn] : tile;
+      const BatchDom &D = sdoms[tile.x];
       const uint32_t k = (uint32_t)tile.y + threadIdx.x;
       if (k < D.cells) {
         int x, y, z;
@@ -95,6 +114,7 @@ __global__ void __launch_bounds__(256) k_batch_persistent(const BatchArgs a) {
                                                 D.kf, nullptr, nullptr, nullptr, D.cells, x,
                                                 y, z);
       }
+      tile = next;
     }
     if (s + 1 < a.nsteps && !grid_barrier(a)) return;
   }
@@ -156,6 +176,80 @@ __global__ void __launch_bounds__(256) k_batch_moments(const BatchArgs a, const 
   }
 }
 
+// f = f^eq(1, u0) on every node of every domain (u0 null: rest). u0 holds
+// dense per-domain blocks: u0[3 * coff + comp * cells + node].
+__global__ void __launch_bounds__(256) k_batch_init_eq(const BatchArgs a, float *f,
+                                                       const float *u0) {
+  const int2 tile = a.tiles[blockIdx.x];
+  const BatchDom &D = a.doms[tile.x];
+  const uint32_t k = (uint32_t)tile.y + threadIdx.x;
+  if (k >= D.cells) return;
+  int x, y, z;
+  decode(D, k, x, y, z);
+  const uint32_t c = ((uint32_t)z * D.ny + y) * D.pitch + x;
+  float ux = 0.f, uy = 0.f, uz = 0.f;
+  if (u0) {
+    const float *ud = u0 + 3 * (size_t)D.coff;
+    ux = ud[k];
+    uy = ud[D.cells + k];
+    uz = ud[2 * (size_t)D.cells + k];
+  }
+  float d[Q];
+  shifted_equilibrium(1.0f, ux, uy, uz, d);
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    f[D.foff + (size_t)i * D.plane + c] = d[i];
+  });
+}
+
+// ---- batched adjoint (one launch per reverse step over the tile table) ----
+
+template <bool GRADF>
+__global__ void __launch_bounds__(256, 3)
+    k_batch_adjoint_step(const BatchArgs a, const float *fn, const float *lam_in,
+                         float *lam_out, float *gF) {
+  const int2 tile = a.tiles[blockIdx.x];
+  const BatchDom &D = a.doms[tile.x];
+  const uint32_t k = (uint32_t)tile.y + threadIdx.x;
+  if (k >= D.cells) return;
+  int x, y, z;
+  decode(D, k, x, y, z);
+  adjoint_node<false, GRADF>(fn + D.foff, lam_in + D.foff, lam_out + D.foff, nullptr,
+                             GRADF ? gF + 3 * (size_t)D.coff : nullptr, D.nx, D.ny, D.nz,
+                             D.pitch, D.plane, D.walls, D.lidc, D.omega, D.kf, D.cells, x, y,
+                             z);
+}
+
+// Seed per node, FP64 loss partial per tile (block) into partials[tile].
+__global__ void __launch_bounds__(256)
+    k_batch_adjoint_seed(const BatchArgs a, const float *fT, const float *ut, float *lam,
+                         float *gF, double *partials) {
+  const int2 tile = a.tiles[blockIdx.x];
+  const BatchDom &D = a.doms[tile.x];
+  const uint32_t k = (uint32_t)tile.y + threadIdx.x;
+  double acc = 0.0;
+  if (k < D.cells) {
+    int x, y, z;
+    decode(D, k, x, y, z);
+    acc = seed_node<false>(fT + D.foff, ut + 3 * (size_t)D.coff, lam + D.foff,
+                           gF ? gF + 3 * (size_t)D.coff : nullptr, nullptr, D.nx, D.ny,
+                           D.pitch, D.plane, D.cells, x, y, z);
+  }
+  if (partials) block_sum_to<256>(acc, partials + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256)
+    k_batch_adjoint_u0(const BatchArgs a, const float *lam0, const float *u0, float *grad) {
+  const int2 tile = a.tiles[blockIdx.x];
+  const BatchDom &D = a.doms[tile.x];
+  const uint32_t k = (uint32_t)tile.y + threadIdx.x;
+  if (k >= D.cells) return;
+  int x, y, z;
+  decode(D, k, x, y, z);
+  u0grad_node(lam0 + D.foff, u0 ? u0 + 3 * (size_t)D.coff : nullptr,
+              grad + 3 * (size_t)D.coff, D.nx, D.ny, D.pitch, D.plane, D.cells, x, y, z);
+}
+
 // ---- launchers ------------------------------------------------------------
 
 const void *batch_persistent_kernel(bool walls) {
@@ -163,12 +257,14 @@ const void *batch_persistent_kernel(bool walls) {
                : (const void *)k_batch_persistent<false>;
 }
 
+size_t batch_persistent_smem(int ndom) { return sizeof(BatchDom) * (size_t)ndom; }
+
 cudaError_t launch_batch_persistent(const BatchArgs &a, int grid, int threads,
                                     cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid, 1, 1);
   cfg.blockDim = dim3(threads, 1, 1);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = batch_persistent_smem(a.ndom);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -197,6 +293,34 @@ cudaError_t launch_batch_rest(const BatchArgs &a, float *f, int threads, cudaStr
 cudaError_t launch_batch_moments(const BatchArgs &a, const float *f, float *rho, float *u,
                                  int threads, cudaStream_t s) {
   k_batch_moments<<<a.ntiles, threads, 0, s>>>(a, f, rho, u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_init_eq(const BatchArgs &a, float *f, const float *u0, int threads,
+                                 cudaStream_t s) {
+  k_batch_init_eq<<<a.ntiles, threads, 0, s>>>(a, f, u0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_adjoint_step(const BatchArgs &a, const float *fn, const float *lam_in,
+                                      float *lam_out, float *gF, int threads, cudaStream_t s) {
+  if (gF)
+    k_batch_adjoint_step<true><<<a.ntiles, threads, 0, s>>>(a, fn, lam_in, lam_out, gF);
+  else
+    k_batch_adjoint_step<false><<<a.ntiles, threads, 0, s>>>(a, fn, lam_in, lam_out, gF);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_adjoint_seed(const BatchArgs &a, const float *fT, const float *ut,
+                                      float *lam, float *gF, double *partials, int threads,
+                                      cudaStream_t s) {
+  k_batch_adjoint_seed<<<a.ntiles, threads, 0, s>>>(a, fT, ut, lam, gF, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_adjoint_u0(const BatchArgs &a, const float *lam0, const float *u0,
+                                    float *grad, int threads, cudaStream_t s) {
+  k_batch_adjoint_u0<<<a.ntiles, threads, 0, s>>>(a, lam0, u0, grad);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,8 @@ struct lbm_batch {
   size_t cells = 0;    // total nodes
   BatchDom *d_doms = nullptr;
   int2 *d_tiles = nullptr;
+  double *d_partials = nullptr;  // one FP64 partial per tile (adjoint loss)
+  double *d_loss_sum = nullptr;
   unsigned *d_bar = nullptr;  // [0] count, [1] generation
   int *d_err = nullptr;
   bool tiles_dirty = true;
@@ -75,8 +77,11 @@ int upload_tables(lbm_batch *b) {
   if (!b->tiles_dirty) return LBM_OK;
   build_tiles(b);
   if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_partials) cudaFree(b->d_partials);
   b->d_tiles = nullptr;
+  b->d_partials = nullptr;
   BCUDA(cudaMalloc(&b->d_tiles, sizeof(int2) * b->tiles.size()), "cudaMalloc tiles");
+  BCUDA(cudaMalloc(&b->d_partials, sizeof(double) * b->tiles.size()), "cudaMalloc partials");
   BCUDA(cudaMemcpy(b->d_tiles, b->tiles.data(), sizeof(int2) * b->tiles.size(),
                    cudaMemcpyHostToDevice), "tile upload");
   b->tiles_dirty = false;
@@ -92,6 +97,7 @@ BatchArgs make_args(const lbm_batch *b) {
   a.doms = b->d_doms;
   a.tiles = b->d_tiles;
   a.ntiles = (int)b->tiles.size();
+  a.ndom = b->ndom;
   a.walls_any = (b->flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z)) != 0;
   a.bar_count = b->d_bar;
   a.bar_gen = b->d_bar + 1;
@@ -105,7 +111,7 @@ int persistent_grid(lbm_batch *b, int *grid) {
   BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &per_sm, lbm::batch_persistent_kernel(
                          (b->flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z)) != 0),
-            b->threads, 0),
+            b->threads, lbm::batch_persistent_smem(b->ndom)),
         "occupancy query");
   if (b->blocks_per_sm > 0 && b->blocks_per_sm < per_sm) per_sm = b->blocks_per_sm;
   int sms = 0;
@@ -130,6 +136,7 @@ int lbm_batch_create(int ndom, const int *dims, const float *tau, const float *l
   if (!out) return bfail(LBM_EINVAL, "out is NULL");
   *out = nullptr;
   if (ndom < 1 || !dims || !tau) return bfail(LBM_EINVAL, "need ndom >= 1, dims, tau");
+  if (ndom > lbm::kMaxBatchDomains) return bfail(LBM_ERANGE, "at most 256 domains per batch");
   const uint32_t known = LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z | LBM_LID;
   if (flags & ~known) return bfail(LBM_EINVAL, "batch supports walls and lid, FP32 only");
   if ((flags & LBM_LID) && !(flags & LBM_WALL_Z)) return bfail(LBM_EINVAL, "LBM_LID needs LBM_WALL_Z");
@@ -155,7 +162,11 @@ int lbm_batch_create(int ndom, const int *dims, const float *tau, const float *l
     D.nx = nx;
     D.ny = ny;
     D.nz = nz;
-    D.pitch = (nx + 7) / 8 * 8;
+    // Unpadded rows: the batch kernels walk each domain's nodes in dense
+    // order, so with pitch = nx every z plane is one contiguous run and no
+    // 32-byte sector is ever partly written (a padded row end would leave a
+    // partial sector that L2 must complete from DRAM on eviction).
+    D.pitch = nx;
     D.plane = (uint32_t)((size_t)D.pitch * ny * nz);
     D.cells = (uint32_t)cells;
     D.foff = foff;
@@ -189,6 +200,7 @@ int lbm_batch_destroy(lbm_batch_t *b) {
   drop_graphs(b);
   if (b->d_doms) cudaFree(b->d_doms);
   if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_partials) cudaFree(b->d_partials);
   if (b->d_bar) cudaFree(b->d_bar);
   if (b->capture) cudaStreamDestroy(b->capture);
   delete b;
@@ -218,10 +230,12 @@ int lbm_batch_bind(lbm_batch_t *b, void *f_a, void *f_b, void *stream) {
     drop_graphs(b);
     if (b->d_doms) cudaFree(b->d_doms);
     if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_partials) cudaFree(b->d_partials);
     if (b->d_bar) cudaFree(b->d_bar);
     if (b->capture) cudaStreamDestroy(b->capture);
     b->d_doms = nullptr;
     b->d_tiles = nullptr;
+    b->d_partials = nullptr;
     b->d_bar = nullptr;
     b->capture = nullptr;
     b->device = dev;
@@ -420,6 +434,65 @@ int lbm_batch_set_f(lbm_batch_t *b, int dom, const double *host_f) {
   BCUDA(cudaMemcpyAsync(b->f[b->cur] + D.foff, stage.data(), stage.size() * sizeof(float),
                         cudaMemcpyHostToDevice, b->stream), "state copy");
   BCUDA(cudaStreamSynchronize(b->stream), "stream sync");
+  return LBM_OK;
+}
+
+int lbm_batch_init_equilibrium(lbm_batch_t *b, const float *u0) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  BCUDA(lbm::launch_batch_init_eq(make_args(b), b->f[b->cur], u0, b->threads, b->stream),
+        "batch init launch");
+  return LBM_OK;
+}
+
+int lbm_batch_step_to(lbm_batch_t *b, const void *f_in, void *f_out) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (!f_in || !f_out || f_in == f_out) return bfail(LBM_EINVAL, "bad buffers");
+  BCUDA(lbm::launch_batch_step(make_args(b), static_cast<const float *>(f_in),
+                               static_cast<float *>(f_out), b->threads, b->stream),
+        "batch step launch");
+  return LBM_OK;
+}
+
+int lbm_batch_adjoint_seed(lbm_batch_t *b, const void *f_T, const float *u_target,
+                           float *lambda_T, float *grad_force, double *loss) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (!f_T || !u_target || !lambda_T) return bfail(LBM_EINVAL, "NULL buffer");
+  BatchArgs a = make_args(b);
+  BCUDA(lbm::launch_batch_adjoint_seed(a, static_cast<const float *>(f_T), u_target, lambda_T,
+                                       grad_force, loss ? b->d_partials : nullptr, b->threads,
+                                       b->stream),
+        "batch seed launch");
+  if (loss) {
+    lbm::Scratch scr;
+    scr.partials = b->d_partials;
+    BCUDA(lbm::launch_finalize_sum(scr, a.ntiles, 0.0, loss, b->stream), "loss reduction");
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_adjoint_step(lbm_batch_t *b, const void *f_n, const float *lambda_in,
+                           float *lambda_out, float *grad_force) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (!f_n || !lambda_in || !lambda_out || lambda_in == lambda_out)
+    return bfail(LBM_EINVAL, "bad buffers");
+  BCUDA(lbm::launch_batch_adjoint_step(make_args(b), static_cast<const float *>(f_n),
+                                       lambda_in, lambda_out, grad_force, b->threads,
+                                       b->stream),
+        "batch adjoint step launch");
+  return LBM_OK;
+}
+
+int lbm_batch_adjoint_u0(lbm_batch_t *b, const float *lambda0, const float *u0,
+                         float *grad_u0) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (!lambda0 || !grad_u0) return bfail(LBM_EINVAL, "NULL buffer");
+  BCUDA(lbm::launch_batch_adjoint_u0(make_args(b), lambda0, u0, grad_u0, b->threads, b->stream),
+        "batch u0 gradient launch");
   return LBM_OK;
 }
 

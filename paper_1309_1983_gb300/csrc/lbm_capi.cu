@@ -99,6 +99,12 @@ int ensure_scratch(lbm_t *h) {
   return LBM_OK;
 }
 
+cudaError_t launch_one_step(const lbm_t *h, bool mom, const StepArgs &a) {
+  if (h->kernel == LBM_KERNEL_PAIR && h->storage != lbm::kF32)
+    return lbm::launch_step_pair16(h->storage, mom, a, h->pbx, h->pby, h->stream);
+  return lbm::launch_step(h->storage, mom, a, h->bx, h->by, h->stream);
+}
+
 int do_steps(lbm_t *h, int n, float *rho, float *u) {
   for (int k = 0; k < n; ++k) {
     StepArgs a = make_args(h, h->f[h->cur], h->f[1 - h->cur]);
@@ -107,7 +113,7 @@ int do_steps(lbm_t *h, int n, float *rho, float *u) {
       a.rho = rho;
       a.u = u;
     }
-    cudaError_t e = lbm::launch_step(h->storage, mom, a, h->bx, h->by, h->stream);
+    cudaError_t e = launch_one_step(h, mom, a);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     h->cur ^= 1;
   }
@@ -199,6 +205,9 @@ int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
   if (by > ny) by = ny;
   h->bx = bx;
   h->by = by < 1 ? 1 : by;
+  h->kernel = LBM_KERNEL_NODE;  // the pair kernel measured slower on GB300
+  h->pbx = 64;
+  h->pby = ny < 4 ? ny : 4;
   h->device = -1;
   *out = h;
   return LBM_OK;
@@ -273,6 +282,25 @@ int lbm_set_block(lbm_t *h, int bx, int by) {
   return LBM_OK;
 }
 
+int lbm_set_kernel(lbm_t *h, int variant) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (variant != LBM_KERNEL_NODE && variant != LBM_KERNEL_PAIR)
+    return fail(LBM_EINVAL, "unknown kernel variant");
+  if (variant == LBM_KERNEL_PAIR && h->storage == lbm::kF32)
+    return fail(LBM_EINVAL, "the pair kernel needs 16-bit storage");
+  h->kernel = variant;
+  return LBM_OK;
+}
+
+int lbm_set_pair_block(lbm_t *h, int bxp, int by) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (bxp < 32 || bxp % 32 != 0 || by < 1 || bxp * by > 256)
+    return fail(LBM_EINVAL, "pair block must be bxp%32==0, by>=1, bxp*by<=256");
+  h->pbx = bxp;
+  h->pby = by;
+  return LBM_OK;
+}
+
 int lbm_current(const lbm_t *h, void **f_cur, void **f_other) {
   int rc = check_bound(h);
   if (rc) return rc;
@@ -311,7 +339,7 @@ int lbm_step_to(lbm_t *h, const void *f_in, void *f_out) {
   if (!aligned(f_in, 256) || !aligned(f_out, 256))
     return fail(LBM_EINVAL, "f buffers must be 256-byte aligned");
   StepArgs a = make_args(h, f_in, f_out);
-  cudaError_t e = lbm::launch_step(h->storage, false, a, h->bx, h->by, h->stream);
+  cudaError_t e = launch_one_step(h, false, a);
   if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
   return LBM_OK;
 }
@@ -460,8 +488,10 @@ int lbm_adjoint_step(lbm_t *h, const void *f_n, const float *lambda_in,
   if (!f_n || !lambda_in || !lambda_out || lambda_in == lambda_out)
     return fail(LBM_EINVAL, "bad buffers");
   StepArgs g = make_args(h, f_n, nullptr);
+  // single-row blocks measured fastest for the adjoint's three node streams
+  const int aby = h->bx >= 128 ? 1 : h->by;
   cudaError_t e = lbm::launch_adjoint_step(g, lambda_in, lambda_out, grad_force,
-                                           h->bx, h->by, h->stream);
+                                           h->bx, aby, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint step launch");
   return LBM_OK;
 }

@@ -17,8 +17,18 @@
 
 namespace lbm {
 
+// Launch bounds of the step kernel. By default only the block size is fixed
+// and ptxas picks the register budget (40 registers for the periodic FP32
+// kernel); defining LBM_STEP_MIN_BLOCKS asks for that many resident 256-thread
+// blocks per SM instead (tuning experiments).
+#ifdef LBM_STEP_MIN_BLOCKS
+#define LBM_STEP_BOUNDS __launch_bounds__(256, LBM_STEP_MIN_BLOCKS)
+#else
+#define LBM_STEP_BOUNDS __launch_bounds__(256)
+#endif
+
 template <int S, bool WALLS, bool FORCE, bool MOM>
-__global__ void __launch_bounds__(256) k_step(const StepArgs a) {
+__global__ void LBM_STEP_BOUNDS k_step(const StepArgs a) {
   using T = typename Store<S>::T;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;

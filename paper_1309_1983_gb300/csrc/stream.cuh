@@ -81,22 +81,26 @@ __device__ __forceinline__ void gather(const typename Store<S>::T *__restrict__ 
   });
 }
 
-// Halfway bounce-back on walled faces: g_i = f_ibar(x) + 6 w_i (e_i . u_w)
-// when x - e_i lies outside a walled axis; u_w is the lid velocity when that
-// source lies on the plane z = nz (e_z = -1 at the top face), folded into
-// lidc[i] = 6 w_i (e_i . u_w) by the host. The wrapped loads this replaces
-// stay in bounds.
+// Pull gather with the halfway bounce-back rule folded into the addresses:
+// d_i = f_i(x - e_i), or f_ibar(x) + 6 w_i (e_i . u_w) when x - e_i lies
+// outside a walled axis; u_w is the lid velocity when that source lies on
+// the plane z = nz (e_z = -1 at the top face), pre-multiplied into
+// lidc[i] = 6 w_i (e_i . u_w) by the host. Each direction is one load whose
+// address is selected per node, so nodes on and off the walls run the same
+// instructions (no divergence in warps that touch a wall).
 template <int S, bool L2ONLY = false>
-__device__ __forceinline__ void bounce_back(const typename Store<S>::T *__restrict__ fin,
-                                            uint32_t plane, const NodeIdx &n,
-                                            const float (&lidc)[Q], float (&d)[Q]) {
+__device__ __forceinline__ void gather_walled(const typename Store<S>::T *__restrict__ fin,
+                                              uint32_t plane, const NodeIdx &n,
+                                              const float (&lidc)[Q], float (&d)[Q]) {
+  d[0] = load_f<S, L2ONLY>(fin + n.c);
   static_for<1, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    if (bounces<i>(n)) {
-      float v = load_f<S, L2ONLY>(fin + (size_t)kOpp_v<i> * plane + n.c);
-      if constexpr (kEz[i] == -1) v += n.z1 ? lidc[i] : 0.0f;
-      d[i] = v;
-    }
+    const bool bb = bounces<i>(n);
+    const size_t idx = bb ? (size_t)kOpp_v<i> * plane + n.c
+                          : (size_t)i * plane + source_of<i>(n);
+    float v = load_f<S, L2ONLY>(fin + idx);
+    if constexpr (kEz[i] == -1) v += n.z1 ? lidc[i] : 0.0f;  // z1 implies bb here
+    d[i] = v;
   });
 }
 
@@ -113,10 +117,10 @@ __device__ __forceinline__ void step_node(
     int z) {
   const NodeIdx n = node_index(nx, ny, nz, pitch, walls, x, y, z);
   float d[Q];
-  gather<S, L2ONLY>(fin, plane, n, d);
-  if constexpr (WALLS) {
-    if (on_wall(n)) bounce_back<S, L2ONLY>(fin, plane, n, lidc, d);
-  }
+  if constexpr (WALLS)
+    gather_walled<S, L2ONLY>(fin, plane, n, lidc, d);
+  else
+    gather<S, L2ONLY>(fin, plane, n, d);
   const uint32_t dc = ((uint32_t)z * ny + y) * nx + x;
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
   if constexpr (FORCE) {

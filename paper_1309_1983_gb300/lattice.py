@@ -113,6 +113,14 @@ class Lattice:
     def set_block(self, bx, by):
         capi.call("lbm_set_block", self._h, int(bx), int(by))
 
+    def set_kernel(self, variant):
+        """"node" (one node per thread) or "pair" (16-bit storage only)."""
+        v = {"node": capi.LBM_KERNEL_NODE, "pair": capi.LBM_KERNEL_PAIR}[variant]
+        capi.call("lbm_set_kernel", self._h, v)
+
+    def set_pair_block(self, bxp, by):
+        capi.call("lbm_set_pair_block", self._h, int(bxp), int(by))
+
     # -- operations -------------------------------------------------------------
     def _field(self, a, comps):
         if a is None:
