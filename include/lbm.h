@@ -134,6 +134,11 @@ int lbm_set_block(lbm_t *h, int bx, int by);
  * propagation the paper measured on Kepler, Sec. 4.3.2). */
 #define LBM_KERNEL_NODE 0
 #define LBM_KERNEL_PAIR 1
+/* LBM_KERNEL_BULK / BULK1: the pulled rows are staged in shared memory by
+ * bulk copies (TMA) in a persistent producer/consumer pipeline (2-row or
+ * 1-row tiles); bit-identical results; lbm_step_moments still uses NODE. */
+#define LBM_KERNEL_BULK 2
+#define LBM_KERNEL_BULK1 3
 int lbm_set_kernel(lbm_t *h, int variant);
 
 /* Block shape of the pair kernel: bxp pairs along x (a multiple of 32) by
@@ -193,7 +198,9 @@ int lbm_moments_noalloc(const void *f, int nx, int ny, int nz, uint32_t flags,
                         const float *force, float *rho, float *u, double *mass,
                         void *stream);
 
-/* Synchronise the bound stream; LBM_ECUDA on a pending CUDA error. */
+/* Synchronise the bound stream; LBM_ECUDA on a pending CUDA error,
+ * LBM_ETIMEOUT if a bounded wait inside a step kernel gave up since the last
+ * check. */
 int lbm_sync(lbm_t *h);
 
 /* Copy the current state to host as FP64 [19][nz][ny][nx], adding w_i back

@@ -36,6 +36,8 @@ LBM_FORCE = 0x40
 LBM_CAVITY = LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z | LBM_LID
 LBM_KERNEL_NODE = 0
 LBM_KERNEL_PAIR = 1
+LBM_KERNEL_BULK = 2
+LBM_KERNEL_BULK1 = 3
 
 
 class LBMError(RuntimeError):

@@ -58,6 +58,7 @@ struct Store<0> {
   using T = float;
   static __device__ __forceinline__ float ld(const T *p) { return __ldg(p); }
   static __device__ __forceinline__ float ld_l2(const T *p) { return __ldcg(p); }
+  static __device__ __forceinline__ float ld_smem(const T *p) { return *p; }
   static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, v); }
 };
 template <>
@@ -69,6 +70,7 @@ struct Store<1> {
   static __device__ __forceinline__ float ld_l2(const T *p) {
     return __half2float(__ldcg(p));
   }
+  static __device__ __forceinline__ float ld_smem(const T *p) { return __half2float(*p); }
   static __device__ __forceinline__ void st(T *p, float v) {
     __stcs(p, __float2half_rn(v));
   }
@@ -82,6 +84,7 @@ struct Store<2> {
   static __device__ __forceinline__ float ld_l2(const T *p) {
     return __bfloat162float(__ldcg(p));
   }
+  static __device__ __forceinline__ float ld_smem(const T *p) { return __bfloat162float(*p); }
   static __device__ __forceinline__ void st(T *p, float v) {
     __stcs(p, __float2bfloat16_rn(v));
   }

@@ -46,6 +46,11 @@ cudaError_t launch_step(int storage, bool moments, const StepArgs &a, int bx,
 // a multiple of 32).
 cudaError_t launch_step_pair16(int storage, bool moments, const StepArgs &a, int bxp, int by,
                                cudaStream_t s);
+// Bulk-copy (TMA) staged step, persistent over tiles; variant 0: 2-row tiles,
+// variant 1: 1-row tiles with a deeper pipeline. err receives kErrTimeout if
+// a bounded mbarrier wait gave up.
+cudaError_t launch_step_bulk(int storage, const StepArgs &a, int *err, int variant, int sms,
+                             cudaStream_t s);
 cudaError_t launch_init(int storage, const StepArgs &a, const float *rho0,
                         const float *u0, int bx, int by, cudaStream_t s);
 // Moments of a stored state into dense rho/u (either may be null); when
@@ -135,7 +140,8 @@ struct lbm_lattice {
   cudaStream_t stream;
   bool bound;
   int bx, by;
-  int kernel;    // LBM_KERNEL_NODE or LBM_KERNEL_PAIR (16-bit storage)
+  int kernel;    // LBM_KERNEL_NODE, LBM_KERNEL_PAIR or LBM_KERNEL_BULK*
+  int sms;       // SM count of the bound device
   int pbx, pby;  // block shape of the pair kernel (pairs along x, rows)
   int device;
   lbm::Scratch scr;

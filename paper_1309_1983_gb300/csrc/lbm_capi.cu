@@ -95,6 +95,7 @@ int ensure_scratch(lbm_t *h) {
   h->scr.err = reinterpret_cast<int *>(h->scr.sum + 1);
   h->scr.nblocks = lbm::kReduceBlocks;
   h->device = dev;
+  LBM_CUDA(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
   LBM_CUDA(cudaMemset(h->scr.err, 0, sizeof(int)), "cudaMemset");
   return LBM_OK;
 }
@@ -102,6 +103,9 @@ int ensure_scratch(lbm_t *h) {
 cudaError_t launch_one_step(const lbm_t *h, bool mom, const StepArgs &a) {
   if (h->kernel == LBM_KERNEL_PAIR && h->storage != lbm::kF32)
     return lbm::launch_step_pair16(h->storage, mom, a, h->pbx, h->pby, h->stream);
+  if ((h->kernel == LBM_KERNEL_BULK || h->kernel == LBM_KERNEL_BULK1) && !mom)
+    return lbm::launch_step_bulk(h->storage, a, h->scr.err,
+                                 h->kernel == LBM_KERNEL_BULK1 ? 1 : 0, h->sms, h->stream);
   return lbm::launch_step(h->storage, mom, a, h->bx, h->by, h->stream);
 }
 
@@ -284,7 +288,8 @@ int lbm_set_block(lbm_t *h, int bx, int by) {
 
 int lbm_set_kernel(lbm_t *h, int variant) {
   if (!h) return fail(LBM_EINVAL, "NULL handle");
-  if (variant != LBM_KERNEL_NODE && variant != LBM_KERNEL_PAIR)
+  if (variant != LBM_KERNEL_NODE && variant != LBM_KERNEL_PAIR && variant != LBM_KERNEL_BULK &&
+      variant != LBM_KERNEL_BULK1)
     return fail(LBM_EINVAL, "unknown kernel variant");
   if (variant == LBM_KERNEL_PAIR && h->storage == lbm::kF32)
     return fail(LBM_EINVAL, "the pair kernel needs 16-bit storage");
@@ -371,8 +376,15 @@ int lbm_moments(lbm_t *h, float *rho, float *u, double *mass) {
 int lbm_sync(lbm_t *h) {
   int rc = check_bound(h);
   if (rc) return rc;
+  int err = 0;
+  LBM_CUDA(cudaMemcpyAsync(&err, h->scr.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+           "error word copy");
   LBM_CUDA(cudaStreamSynchronize(h->stream), "stream sync");
   LBM_CUDA(cudaGetLastError(), "pending error");
+  if (err & lbm::kErrTimeout) {
+    LBM_CUDA(cudaMemset(h->scr.err, 0, sizeof(int)), "error word clear");
+    return fail(LBM_ETIMEOUT, "a bounded wait in a step kernel gave up");
+  }
   return LBM_OK;
 }
 

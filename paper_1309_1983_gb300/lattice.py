@@ -114,8 +114,10 @@ class Lattice:
         capi.call("lbm_set_block", self._h, int(bx), int(by))
 
     def set_kernel(self, variant):
-        """"node" (one node per thread) or "pair" (16-bit storage only)."""
-        v = {"node": capi.LBM_KERNEL_NODE, "pair": capi.LBM_KERNEL_PAIR}[variant]
+        """"node" (one node per thread), "pair" (16-bit storage only), or
+        "bulk" / "bulk1" (rows staged in shared memory by bulk copies)."""
+        v = {"node": capi.LBM_KERNEL_NODE, "pair": capi.LBM_KERNEL_PAIR,
+             "bulk": capi.LBM_KERNEL_BULK, "bulk1": capi.LBM_KERNEL_BULK1}[variant]
         capi.call("lbm_set_kernel", self._h, v)
 
     def set_pair_block(self, bxp, by):
