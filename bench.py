@@ -44,7 +44,8 @@ def parse():
     p.add_argument("--n", type=int, default=N_DEFAULT, help="lattice edge (cube)")
     p.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     p.add_argument("--extras", default="all",
-                   help="comma list of secondary workloads: storage,adjoint,batched (or all)")
+                   help="comma list of secondary workloads: storage,streaming,adjoint,batched "
+                        "(or all)")
     p.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                    help="storage of the main timed workload (profiling runs)")
     p.add_argument("--geometry", default="periodic", choices=["periodic", "cavity"],
@@ -269,6 +270,41 @@ def extra_workloads(torch, n, steps=100, warmup=10):
     return out
 
 
+def streaming_ablation(torch, n, steps=50):
+    """Sec. 4.3 redone on this GPU: streaming alone as an unshifted copy, a
+    gather (misaligned reads) and a scatter (misaligned writes), and the full
+    step in pull order (Alg. 3) and push order (Alg. 2); FP32, periodic."""
+    from paper_1309_1983_gb300.lattice import Lattice
+    L = Lattice(n, n, n, TAU)
+    L.init_equilibrium()
+    a, b = L.current_buffers()
+    s = L.stream
+    out = {}
+    cases = (("copy", lambda x, y: L.streaming(x, y, "copy")),
+             ("stream_gather", lambda x, y: L.streaming(x, y, "pull")),
+             ("stream_scatter", lambda x, y: L.streaming(x, y, "push")),
+             ("step_pull", lambda x, y: L.step_to(x, y)),
+             ("step_push", lambda x, y: L.step_push(x, y)))
+    for name, fn in cases:
+        for _ in range(3):
+            fn(a, b)
+            a, b = b, a
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            fn(a, b)
+            a, b = b, a
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"mlups": round(n ** 3 / ms / 1e3, 1),
+                     "gbs": round(152 * n ** 3 / (ms / 1e3) / 1e9, 1)}
+    L.close()
+    del L
+    torch.cuda.empty_cache()
+    return out
+
+
 def adjoint_workload(torch, n=128, T=500, K=50, tau=0.7):
     """Periodic 128^3, tau = 0.7, u0 and u_target random Fourier modes
     (|k| <= 4, amplitude 0.02, seeds 1 and 2), F = 0, T = 500, checkpoints
@@ -478,10 +514,12 @@ def run_ours(args):
         del L, u0
         torch.cuda.empty_cache()
         want = set(args.extras.split(",")) if args.extras != "all" else {
-            "storage", "adjoint", "batched"}
+            "storage", "streaming", "adjoint", "batched"}
         extras = {}
         if "storage" in want:
             extras.update(extra_workloads(torch, n))
+        if "streaming" in want:
+            extras["streaming"] = streaming_ablation(torch, n)
         if "adjoint" in want:
             extras["adjoint"] = adjoint_workload(torch, n=args.adj_n, T=args.adj_steps)
         if "batched" in want:
@@ -520,6 +558,8 @@ def run_ours(args):
         "per_step_mlups": {"mean": round(statistics.mean(mlups_each), 1),
                            "stdev": round(statistics.pstdev(mlups_each), 1),
                            "best": round(max(mlups_each), 1)},
+        "step_time_spectrum": dict(zip(("peak_hz", "peak_amplitude_ms", "resolution_hz"),
+                                       PM.step_time_spectrum(per))),
         "per_rank_mlups": round(per_rank_mlups, 1),
         "mass_rel_drift": mass_rel,
         "clocks": clocks,

@@ -167,6 +167,25 @@ int lbm_step_moments(lbm_t *h, int n, float *rho, float *u);
  * current-state pointer are not touched. */
 int lbm_step_to(lbm_t *h, const void *f_in, void *f_out);
 
+/* Push iteration (Alg. 2) for the streaming-order comparison of Sec. 4.2:
+ * g_in and g_out hold POST-STREAMING distributions (layout and storage as
+ * the f buffers); each node reads its own values (aligned), collides, and
+ * writes f*_i to x + e_i (misaligned writes for e_x != 0), or back as the
+ * opposite direction at x, plus the moving-wall term, when x + e_i lies
+ * outside a walled axis. Starting from g^0 = P f^0 (P: lbm_stream, form
+ * PULL) the push states are P applied to the pull states. */
+int lbm_step_push(lbm_t *h, const void *g_in, void *g_out);
+
+/* Streaming alone, f_out = P f_in (boundary rule included): form
+ * LBM_STREAM_PULL gathers (misaligned reads, aligned writes),
+ * LBM_STREAM_PUSH scatters (aligned reads, misaligned writes); both give the
+ * same result. LBM_STREAM_COPY copies the 19 planes unshifted (the
+ * bandwidth reference of the aligned/misaligned comparison, Sec. 4.3). */
+#define LBM_STREAM_PULL 0
+#define LBM_STREAM_PUSH 1
+#define LBM_STREAM_COPY 2
+int lbm_stream(lbm_t *h, const void *f_in, void *f_out, int form);
+
 /* Moments of the current (post-collision) state: rho = sum f_i (Eq. 6),
  * u = (sum e_i f_i - F/2)/rho (Eq. 7 with the half-force correction), into
  * device FP32 fields (either may be NULL). If mass != NULL the call also
@@ -207,15 +226,22 @@ int lbm_sync(lbm_t *h);
  * (the plain f_i). Synchronous. */
 int lbm_get_f(lbm_t *h, double *host_f);
 
+/* As lbm_get_f for any device buffer `buf` in the handle's f layout. */
+int lbm_get_buffer(lbm_t *h, const void *buf, double *host_f);
+
 /* Set the current state from host FP64 [19][nz][ny][nx] (plain f_i; the
  * library subtracts w_i and rounds to the storage type). Synchronous. */
 int lbm_set_f(lbm_t *h, const double *host_f);
 
 /* End-to-end call on host buffers: copy u0 [3][nz][ny][nx] (host FP32,
- * ideally pinned) to the device, set the state to f^eq(1, u0), advance n >= 1
- * steps, and copy rho [nz][ny][nx] and u [3][nz][ny][nx] of the final state
- * back to host. The non-current f buffer is used as staging for the copies
- * (it is scratch between steps by design). Synchronous. */
+ * pinned for asynchronous copies; NULL = rest) to the device, set the state
+ * to f^eq(1, u0), advance n >= 1 steps, and copy rho [nz][ny][nx] and
+ * u [3][nz][ny][nx] of the final state back to host. The transfers are
+ * pipelined by z slabs on two copy streams: each slab is initialised as soon
+ * as it has arrived, and each slab of the last step is copied out as soon as
+ * its moments are done. On first use the handle allocates its device staging
+ * (28 bytes per node), two streams and a few events, released by lbm_destroy.
+ * Synchronous. */
 int lbm_run_host(lbm_t *h, const float *u0_host, int n, float *rho_host,
                  float *u_host);
 

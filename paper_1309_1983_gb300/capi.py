@@ -34,6 +34,9 @@ LBM_STORE_F16 = 0x10
 LBM_STORE_BF16 = 0x20
 LBM_FORCE = 0x40
 LBM_CAVITY = LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z | LBM_LID
+LBM_STREAM_PULL = 0
+LBM_STREAM_PUSH = 1
+LBM_STREAM_COPY = 2
 LBM_KERNEL_NODE = 0
 LBM_KERNEL_PAIR = 1
 LBM_KERNEL_BULK = 2
@@ -79,10 +82,13 @@ _SIGNATURES = {
     "lbm_step": [_vp, _i],
     "lbm_step_moments": [_vp, _i, _vp, _vp],
     "lbm_step_to": [_vp, _vp, _vp],
+    "lbm_step_push": [_vp, _vp, _vp],
+    "lbm_stream": [_vp, _vp, _vp, _i],
     "lbm_moments": [_vp, _vp, _vp, _dp],
     "lbm_moments_noalloc": [_vp, _i, _i, _i, _u32, _vp, _vp, _vp, _vp, _vp],
     "lbm_sync": [_vp],
     "lbm_get_f": [_vp, _vp],
+    "lbm_get_buffer": [_vp, _vp, _vp],
     "lbm_set_f": [_vp, _vp],
     "lbm_run_host": [_vp, _vp, _i, _vp, _vp],
     "lbm_adjoint_seed": [_vp, _vp, _vp, _vp, _vp, _vp],

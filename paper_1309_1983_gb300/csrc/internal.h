@@ -23,6 +23,7 @@ struct StepArgs {
   float omega, kf;     // 1/tau and 1 - 1/(2 tau)
   uint32_t walls;      // LBM_WALL_* bits
   float lidc[19];      // 6 w_i (e_i . u_w) for sources on z = nz (else 0)
+  int z0, zn;          // planes [z0, z0 + zn) processed by a launch (0, nz: all)
 };
 
 struct Scratch {
@@ -51,6 +52,11 @@ cudaError_t launch_step_pair16(int storage, bool moments, const StepArgs &a, int
 // a bounded mbarrier wait gave up.
 cudaError_t launch_step_bulk(int storage, const StepArgs &a, int *err, int variant, int sms,
                              cudaStream_t s);
+// Push iteration (Alg. 2) on post-streaming states, and streaming alone
+// (form 0 gather, 1 scatter, 2 unshifted copy).
+cudaError_t launch_step_push(int storage, const StepArgs &a, int bx, int by, cudaStream_t s);
+cudaError_t launch_stream(int storage, const StepArgs &a, int form, int bx, int by,
+                          cudaStream_t s);
 cudaError_t launch_init(int storage, const StepArgs &a, const float *rho0,
                         const float *u0, int bx, int by, cudaStream_t s);
 // Moments of a stored state into dense rho/u (either may be null); when
@@ -145,4 +151,10 @@ struct lbm_lattice {
   int pbx, pby;  // block shape of the pair kernel (pairs along x, rows)
   int device;
   lbm::Scratch scr;
+  // lbm_run_host pipeline (created on first use, released by lbm_destroy)
+  static constexpr int kMaxSlabs = 8;
+  cudaStream_t copy_in, copy_out;
+  cudaEvent_t ev_start, ev_in[kMaxSlabs], ev_out[kMaxSlabs], ev_done;
+  float *stage;  // 3 cells (u0) + 4 cells (rho, u) FP32
+  bool pipe_ready;
 };

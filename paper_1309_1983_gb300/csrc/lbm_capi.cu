@@ -56,6 +56,8 @@ StepArgs make_args(const lbm_t *h, const void *fin, void *fout) {
   a.omega = 1.0f / h->tau;
   a.kf = 1.0f - 0.5f * a.omega;
   a.walls = h->flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z);
+  a.z0 = 0;
+  a.zn = h->nz;
   for (int i = 0; i < lbm::Q; ++i) {
     a.lidc[i] = 0.0f;
     if ((h->flags & LBM_LID) && lbm::kEz[i] == -1)
@@ -107,6 +109,45 @@ cudaError_t launch_one_step(const lbm_t *h, bool mom, const StepArgs &a) {
     return lbm::launch_step_bulk(h->storage, a, h->scr.err,
                                  h->kernel == LBM_KERNEL_BULK1 ? 1 : 0, h->sms, h->stream);
   return lbm::launch_step(h->storage, mom, a, h->bx, h->by, h->stream);
+}
+
+// Streams, events and staging of lbm_run_host, created on first use.
+int ensure_pipeline(lbm_t *h) {
+  if (h->pipe_ready) return LBM_OK;
+  const size_t cells = (size_t)h->nx * h->ny * h->nz;
+  if (cudaMalloc(&h->stage, 7 * cells * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    h->stage = nullptr;
+    return fail(LBM_ENOMEM, "cudaMalloc of the host-transfer staging failed");
+  }
+  LBM_CUDA(cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking), "stream create");
+  LBM_CUDA(cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking), "stream create");
+  LBM_CUDA(cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming), "event create");
+  LBM_CUDA(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming), "event create");
+  for (int k = 0; k < lbm_lattice::kMaxSlabs; ++k) {
+    LBM_CUDA(cudaEventCreateWithFlags(&h->ev_in[k], cudaEventDisableTiming), "event create");
+    LBM_CUDA(cudaEventCreateWithFlags(&h->ev_out[k], cudaEventDisableTiming), "event create");
+  }
+  h->pipe_ready = true;
+  return LBM_OK;
+}
+
+void release_pipeline(lbm_t *h) {
+  if (!h->pipe_ready) {
+    if (h->stage) cudaFree(h->stage);
+    return;
+  }
+  cudaFree(h->stage);
+  cudaStreamDestroy(h->copy_in);
+  cudaStreamDestroy(h->copy_out);
+  cudaEventDestroy(h->ev_start);
+  cudaEventDestroy(h->ev_done);
+  for (int k = 0; k < lbm_lattice::kMaxSlabs; ++k) {
+    cudaEventDestroy(h->ev_in[k]);
+    cudaEventDestroy(h->ev_out[k]);
+  }
+  h->pipe_ready = false;
+  h->stage = nullptr;
 }
 
 int do_steps(lbm_t *h, int n, float *rho, float *u) {
@@ -213,12 +254,15 @@ int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
   h->pbx = 64;
   h->pby = ny < 4 ? ny : 4;
   h->device = -1;
+  h->stage = nullptr;
+  h->pipe_ready = false;
   *out = h;
   return LBM_OK;
 }
 
 int lbm_destroy(lbm_t *h) {
   if (!h) return LBM_OK;
+  release_pipeline(h);
   if (h->scr.partials) cudaFree(h->scr.partials);
   delete h;
   return LBM_OK;
@@ -349,6 +393,31 @@ int lbm_step_to(lbm_t *h, const void *f_in, void *f_out) {
   return LBM_OK;
 }
 
+int lbm_step_push(lbm_t *h, const void *g_in, void *g_out) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (!g_in || !g_out || g_in == g_out) return fail(LBM_EINVAL, "bad buffers");
+  if (!aligned(g_in, 256) || !aligned(g_out, 256))
+    return fail(LBM_EINVAL, "buffers must be 256-byte aligned");
+  StepArgs a = make_args(h, g_in, g_out);
+  cudaError_t e = lbm::launch_step_push(h->storage, a, h->bx, h->by, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "push step launch");
+  return LBM_OK;
+}
+
+int lbm_stream(lbm_t *h, const void *f_in, void *f_out, int form) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (!f_in || !f_out || f_in == f_out) return fail(LBM_EINVAL, "bad buffers");
+  if (form < LBM_STREAM_PULL || form > LBM_STREAM_COPY) return fail(LBM_EINVAL, "bad form");
+  if (!aligned(f_in, 256) || !aligned(f_out, 256))
+    return fail(LBM_EINVAL, "buffers must be 256-byte aligned");
+  StepArgs a = make_args(h, f_in, f_out);
+  cudaError_t e = lbm::launch_stream(h->storage, a, form, h->bx, h->by, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream kernel launch");
+  return LBM_OK;
+}
+
 int lbm_moments(lbm_t *h, float *rho, float *u, double *mass) {
   int rc = check_bound(h);
   if (rc) return rc;
@@ -391,12 +460,17 @@ int lbm_sync(lbm_t *h) {
 int lbm_get_f(lbm_t *h, double *host_f) {
   int rc = check_bound(h);
   if (rc) return rc;
-  if (!host_f) return fail(LBM_EINVAL, "host_f is NULL");
+  return lbm_get_buffer(h, h->f[h->cur], host_f);
+}
+
+int lbm_get_buffer(lbm_t *h, const void *buf, double *host_f) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (!host_f || !buf) return fail(LBM_EINVAL, "NULL buffer");
   const size_t bytes = (size_t)lbm::Q * h->plane * h->elem_bytes;
   void *stage = malloc(bytes);
   if (!stage) return fail(LBM_ENOMEM, "host staging allocation failed");
-  cudaError_t e = cudaMemcpyAsync(stage, h->f[h->cur], bytes,
-                                  cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e = cudaMemcpyAsync(stage, buf, bytes, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     free(stage);
@@ -448,27 +522,67 @@ int lbm_run_host(lbm_t *h, const float *u0_host, int n, float *rho_host,
   int rc = check_bound(h);
   if (rc) return rc;
   if (n < 1 || !rho_host || !u_host) return fail(LBM_EINVAL, "need n >= 1, rho, u");
+  rc = ensure_pipeline(h);
+  if (rc) return rc;
   const size_t cells = (size_t)h->nx * h->ny * h->nz;
-  // the f buffer is at least 38 * cells bytes; u0 needs 12, rho + u need 16
-  float *stage = static_cast<float *>(h->f[1 - h->cur]);
-  const float *u0d = nullptr;
-  if (u0_host) {
-    LBM_CUDA(cudaMemcpyAsync(stage, u0_host, 3 * cells * sizeof(float),
-                             cudaMemcpyHostToDevice, h->stream), "u0 copy");
-    u0d = stage;
+  const size_t nxy = (size_t)h->nx * h->ny;
+  const int S = h->nz < lbm_lattice::kMaxSlabs ? h->nz : lbm_lattice::kMaxSlabs;
+  int zs[lbm_lattice::kMaxSlabs + 1];
+  for (int k = 0; k <= S; ++k) zs[k] = (int)((long long)k * h->nz / S);
+  float *u0d = h->stage;            // 3 * cells
+  float *rd = h->stage + 3 * cells;  // cells
+  float *ud = rd + cells;            // 3 * cells
+  // the copy streams start after the work already queued on the handle's stream
+  LBM_CUDA(cudaEventRecord(h->ev_start, h->stream), "event record");
+  LBM_CUDA(cudaStreamWaitEvent(h->copy_in, h->ev_start, 0), "stream wait");
+  LBM_CUDA(cudaStreamWaitEvent(h->copy_out, h->ev_start, 0), "stream wait");
+  // 1. copy u0 in by z slabs; each slab is initialised as soon as it arrives
+  for (int k = 0; k < S; ++k) {
+    if (u0_host) {
+      const size_t off = (size_t)zs[k] * nxy, len = (size_t)(zs[k + 1] - zs[k]) * nxy;
+      for (int c = 0; c < 3; ++c)
+        LBM_CUDA(cudaMemcpyAsync(u0d + c * cells + off, u0_host + c * cells + off,
+                                 len * sizeof(float), cudaMemcpyHostToDevice, h->copy_in),
+                 "u0 copy");
+    }
+    LBM_CUDA(cudaEventRecord(h->ev_in[k], h->copy_in), "event record");
+    LBM_CUDA(cudaStreamWaitEvent(h->stream, h->ev_in[k], 0), "stream wait");
+    StepArgs a = make_args(h, nullptr, h->f[h->cur]);
+    a.z0 = zs[k];
+    a.zn = zs[k + 1] - zs[k];
+    cudaError_t e = lbm::launch_init(h->storage, a, nullptr, u0_host ? u0d : nullptr, h->bx,
+                                     h->by, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "init kernel launch");
   }
-  rc = lbm_init_equilibrium(h, nullptr, u0d);
+  // 2. all but the last step over the whole lattice
+  rc = do_steps(h, n - 1, nullptr, nullptr);
   if (rc) return rc;
-  rc = do_steps(h, n, nullptr, nullptr);
-  if (rc) return rc;
-  float *rd = static_cast<float *>(h->f[1 - h->cur]);
-  float *ud = rd + cells;
-  rc = lbm_moments(h, rd, ud, nullptr);
-  if (rc) return rc;
-  LBM_CUDA(cudaMemcpyAsync(rho_host, rd, cells * sizeof(float),
-                           cudaMemcpyDeviceToHost, h->stream), "rho copy");
-  LBM_CUDA(cudaMemcpyAsync(u_host, ud, 3 * cells * sizeof(float),
-                           cudaMemcpyDeviceToHost, h->stream), "u copy");
+  // 3. the last step and the moments by z slabs; each slab is copied out as
+  //    soon as its moments are done
+  for (int k = 0; k < S; ++k) {
+    StepArgs a = make_args(h, h->f[h->cur], h->f[1 - h->cur]);
+    a.z0 = zs[k];
+    a.zn = zs[k + 1] - zs[k];
+    cudaError_t e = lbm::launch_step(h->storage, false, a, h->bx, h->by, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+    StepArgs m = make_args(h, nullptr, nullptr);
+    m.z0 = a.z0;
+    m.zn = a.zn;
+    e = lbm::launch_moments(h->storage, m, h->f[1 - h->cur], rd, ud, nullptr, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moments kernel launch");
+    LBM_CUDA(cudaEventRecord(h->ev_out[k], h->stream), "event record");
+    LBM_CUDA(cudaStreamWaitEvent(h->copy_out, h->ev_out[k], 0), "stream wait");
+    const size_t off = (size_t)zs[k] * nxy, len = (size_t)(zs[k + 1] - zs[k]) * nxy;
+    LBM_CUDA(cudaMemcpyAsync(rho_host + off, rd + off, len * sizeof(float),
+                             cudaMemcpyDeviceToHost, h->copy_out), "rho copy");
+    for (int c = 0; c < 3; ++c)
+      LBM_CUDA(cudaMemcpyAsync(u_host + c * cells + off, ud + c * cells + off,
+                               len * sizeof(float), cudaMemcpyDeviceToHost, h->copy_out),
+               "u copy");
+  }
+  h->cur ^= 1;
+  LBM_CUDA(cudaEventRecord(h->ev_done, h->copy_out), "event record");
+  LBM_CUDA(cudaStreamWaitEvent(h->stream, h->ev_done, 0), "stream wait");
   LBM_CUDA(cudaStreamSynchronize(h->stream), "stream sync");
   return LBM_OK;
 }

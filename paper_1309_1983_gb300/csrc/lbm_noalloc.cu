@@ -88,6 +88,8 @@ extern "C" int lbm_moments_noalloc(const void *f, int nx, int ny, int nz, uint32
   a.pitch = (int)pitch;
   a.plane = (uint32_t)plane;
   a.cells = cells;
+  a.z0 = 0;
+  a.zn = nz;
   a.force = (flags & LBM_FORCE) ? force : nullptr;
 
   lbm::Scratch scr;

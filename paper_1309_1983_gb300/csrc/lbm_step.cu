@@ -32,7 +32,7 @@ __global__ void LBM_STEP_BOUNDS k_step(const StepArgs a) {
   using T = typename Store<S>::T;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = a.z0 + blockIdx.z;
   if (x >= a.nx || y >= a.ny) return;
   step_node<S, WALLS, FORCE, MOM, false>(
       static_cast<const T *>(a.fin), static_cast<T *>(a.fout), a.nx, a.ny, a.nz, a.pitch,
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256)
   using T = typename Store<S>::T;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = a.z0 + blockIdx.z;
   if (x >= a.nx || y >= a.ny) return;
   const uint32_t c = ((uint32_t)z * a.ny + y) * a.pitch + x;
   const uint32_t dc = ((uint32_t)z * a.ny + y) * a.nx + x;
@@ -77,8 +77,10 @@ __global__ void __launch_bounds__(kReduceThreads)
   const T *__restrict__ f = static_cast<const T *>(fv);
   double acc = 0.0;
   bool bad = false;
-  for (uint32_t dc = blockIdx.x * blockDim.x + threadIdx.x; dc < a.cells;
-       dc += gridDim.x * blockDim.x) {
+  const uint32_t plane_nodes = (uint32_t)a.nx * a.ny;
+  const uint32_t dc_end = (uint32_t)(a.z0 + a.zn) * plane_nodes;
+  for (uint32_t dc = (uint32_t)a.z0 * plane_nodes + blockIdx.x * blockDim.x + threadIdx.x;
+       dc < dc_end; dc += gridDim.x * blockDim.x) {
     const uint32_t x = dc % a.nx;
     const uint32_t t = dc / a.nx;
     const uint32_t y = t % a.ny, z = t / a.ny;
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(1024)
 // ---- launchers ---------------------------------------------------------------
 
 static dim3 node_grid(const StepArgs &a, int bx, int by) {
-  return dim3((a.nx + bx - 1) / bx, (a.ny + by - 1) / by, a.nz);
+  return dim3((a.nx + bx - 1) / bx, (a.ny + by - 1) / by, a.zn);
 }
 
 template <int S>
@@ -200,7 +202,8 @@ static void moments_dispatch(const StepArgs &a, const void *f, float *rho,
 cudaError_t launch_moments(int storage, const StepArgs &a, const void *f,
                            float *rho, float *u, const Scratch *scr,
                            cudaStream_t s) {
-  int nb = (int)((a.cells + kReduceThreads - 1) / kReduceThreads);
+  const uint32_t nodes = (uint32_t)a.zn * a.nx * a.ny;
+  int nb = (int)((nodes + kReduceThreads - 1) / kReduceThreads);
   if (nb > kReduceBlocks) nb = kReduceBlocks;
   if (nb < 1) nb = 1;
   double *partials = scr ? scr->partials : nullptr;

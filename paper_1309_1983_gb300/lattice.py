@@ -151,6 +151,23 @@ class Lattice:
     def step_to(self, f_in, f_out):
         capi.call("lbm_step_to", self._h, _ptr(f_in), _ptr(f_out))
 
+    def step_push(self, g_in, g_out):
+        """One push step (Alg. 2) on post-streaming states."""
+        capi.call("lbm_step_push", self._h, _ptr(g_in), _ptr(g_out))
+
+    def streaming(self, f_in, f_out, form="pull"):
+        """f_out = P f_in; form "pull", "push" or "copy" (unshifted)."""
+        v = {"pull": capi.LBM_STREAM_PULL, "push": capi.LBM_STREAM_PUSH,
+             "copy": capi.LBM_STREAM_COPY}[form]
+        capi.call("lbm_stream", self._h, _ptr(f_in), _ptr(f_out), v)
+
+    def buffer_to_numpy(self, buf):
+        """Any device f buffer of this lattice as FP64 (19, nz, ny, nx) plain
+        values (as get_f for the current state)."""
+        out = np.empty((19,) + self.shape, dtype=np.float64)
+        capi.call("lbm_get_buffer", self._h, _ptr(buf), out.ctypes.data_as(ctypes.c_void_p))
+        return out
+
     def moments(self, mass=False):
         """(rho, u) of the current state as device tensors; with mass=True
         also the FP64 total mass (synchronises)."""

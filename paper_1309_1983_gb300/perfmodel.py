@@ -46,3 +46,26 @@ def achieved_gbs(mlups: float, bytes_per_lu: float) -> float:
 def reynolds(u: float, tau: float, L: float) -> float:
     """Eq. 8 solved for Re: u = (tau - 1/2) Re / (3 L)."""
     return 3.0 * L * u / (tau - 0.5)
+
+
+def step_time_spectrum(step_ms):
+    """Periodic variation of per-iteration times (the Fourier analysis of
+    Sec. 6 / Table 5). The series is taken at the iterations' own (uneven)
+    completion times, resampled to a uniform grid of the mean step length,
+    detrended, and its amplitude spectrum computed with an FFT. Returns
+    (peak frequency in Hz, peak amplitude in ms, frequency resolution in Hz);
+    (None, None, None) for fewer than 16 iterations."""
+    import numpy as np
+
+    t = np.asarray(step_ms, dtype=np.float64)
+    if t.size < 16:
+        return None, None, None
+    when = np.cumsum(t) / 1e3  # completion times in s
+    dt = float(t.mean()) / 1e3
+    grid = when[0] + dt * np.arange(t.size)
+    x = np.interp(grid, when, t)
+    x = x - np.polyval(np.polyfit(grid, x, 1), grid)
+    amp = np.abs(np.fft.rfft(x)) * 2.0 / x.size
+    freq = np.fft.rfftfreq(x.size, d=dt)
+    k = int(np.argmax(amp[1:]) + 1)
+    return float(freq[k]), float(amp[k]), float(freq[1])

@@ -290,3 +290,48 @@ def test_bulk_kernel_is_bit_identical_to_node_kernel(storage, variant, geom, sha
         L.sync()
         outs.append(L.get_f())
     np.testing.assert_array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("geom", sorted(GEOMS))
+@pytest.mark.parametrize("shape", [(37, 11, 9), (1, 7, 6), (5, 1, 1)], ids=lambda s: "x".join(map(str, s)))
+def test_streaming_forms_equal_oracle_stream(geom, shape):
+    """lbm_stream: the gather (pull) and scatter (push) forms both equal the
+    oracle's stream pass (boundary rule included); the copy form is the
+    identity."""
+    nx, ny, nz = shape
+    g = GEOMS[geom]
+    L = _lat(nx, ny, nz, 0.7, g["walls"], g["lid"])
+    OL = _olat(nx, ny, nz, 0.7, g["walls"], g["lid"])
+    f0 = _random_state(OL, 8)
+    L.set_f(f0)
+    cur, _ = L.current_buffers()
+    ref = O.stream(OL, L.get_f())
+    out = torch.empty_like(cur)
+    for form in ("pull", "push"):
+        L.streaming(cur, out, form)
+        assert np.abs(L.buffer_to_numpy(out) - ref).max() <= 1e-7, form
+    L.streaming(cur, out, "copy")
+    np.testing.assert_array_equal(L.buffer_to_numpy(out), L.get_f())
+
+
+@pytest.mark.parametrize("geom", sorted(GEOMS))
+@pytest.mark.parametrize("force", [False, True])
+def test_push_iteration_tracks_streamed_pull_states(geom, force):
+    """Alg. 2 (push) from g^0 = P f^0 gives g^n = P f^n after n steps, f^n
+    the oracle's pull states (Alg. 3): the two orders compute the same
+    method."""
+    nx, ny, nz = 23, 9, 7
+    g = GEOMS[geom]
+    L = _lat(nx, ny, nz, 0.65, g["walls"], g["lid"], force=force)
+    OL = _olat(nx, ny, nz, 0.65, g["walls"], g["lid"])
+    F = W.noise((3,) + OL.shape, 9, 1e-3) if force else None
+    if force:
+        L.force.copy_(torch.from_numpy(F).float())
+    f0 = _random_state(OL, 12)
+    L.set_f(O.stream(OL, f0))
+    a, b = L.current_buffers()
+    for _ in range(4):
+        L.step_push(a, b)
+        a, b = b, a
+    ref = O.stream(OL, O.run(OL, f0, 4, F))
+    assert np.abs(L.buffer_to_numpy(a) - ref).max() <= ATOL_F

@@ -38,3 +38,14 @@ def test_printed_limits(golden_dir):
 def test_reynolds_eq8():
     # Eq. 8 inverted: the 32^3 cavity at tau = 0.6 with lid 0.05 is Re = 48
     assert abs(PM.reynolds(0.05, 0.6, 32) - 48.0) < 1e-12
+
+
+def test_step_time_spectrum_finds_a_planted_period():
+    import numpy as np
+    rng = np.random.default_rng(0)
+    n, base = 2000, 1.25  # ms per step, like the 384^3 step
+    t_s = np.arange(n) * base / 1e3
+    step = base + 0.02 * np.sin(2 * np.pi * 11.7 * t_s) + 0.002 * rng.standard_normal(n)
+    f, a, res = PM.step_time_spectrum(step)
+    assert abs(f - 11.7) <= res and 0.015 < a < 0.025
+    assert PM.step_time_spectrum([1.0] * 5) == (None, None, None)
