@@ -141,6 +141,19 @@ int lbm_set_block(lbm_t *h, int bx, int by);
 #define LBM_KERNEL_BULK1 3
 int lbm_set_kernel(lbm_t *h, int variant);
 
+/* How the one-node kernel applies bounce-back: LBM_WALLS_SELECT picks each
+ * direction's load address (pulled neighbour or opposite direction at the
+ * node) for every node, with no divergence; LBM_WALLS_BRANCH gathers as if
+ * periodic and re-reads the bounced directions only on wall nodes (fewer
+ * instructions when wall nodes are rare in each warp). LBM_WALLS_AUTO
+ * (default) selects for FP32 storage and for rows shorter than 256 nodes,
+ * else branches. The results are identical. Returns LBM_EINVAL for any
+ * other mode. */
+#define LBM_WALLS_AUTO 0
+#define LBM_WALLS_BRANCH 1
+#define LBM_WALLS_SELECT 2
+int lbm_set_wall_mode(lbm_t *h, int mode);
+
 /* Block shape of the pair kernel: bxp pairs along x (a multiple of 32) by
  * `by` rows, bxp * by <= 256. Default: 64 x 4 (or fewer rows for small ny). */
 int lbm_set_pair_block(lbm_t *h, int bxp, int by);

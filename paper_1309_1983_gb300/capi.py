@@ -34,6 +34,9 @@ LBM_STORE_F16 = 0x10
 LBM_STORE_BF16 = 0x20
 LBM_FORCE = 0x40
 LBM_CAVITY = LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z | LBM_LID
+LBM_WALLS_AUTO = 0
+LBM_WALLS_BRANCH = 1
+LBM_WALLS_SELECT = 2
 LBM_STREAM_PULL = 0
 LBM_STREAM_PUSH = 1
 LBM_STREAM_COPY = 2
@@ -77,6 +80,7 @@ _SIGNATURES = {
     "lbm_set_block": [_vp, _i, _i],
     "lbm_set_kernel": [_vp, _i],
     "lbm_set_pair_block": [_vp, _i, _i],
+    "lbm_set_wall_mode": [_vp, _i],
     "lbm_current": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "lbm_init_equilibrium": [_vp, _vp, _vp],
     "lbm_step": [_vp, _i],

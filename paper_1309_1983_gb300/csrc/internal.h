@@ -24,6 +24,7 @@ struct StepArgs {
   uint32_t walls;      // LBM_WALL_* bits
   float lidc[19];      // 6 w_i (e_i . u_w) for sources on z = nz (else 0)
   int z0, zn;          // planes [z0, z0 + zn) processed by a launch (0, nz: all)
+  int wall_select;     // 1: per-direction address select, 0: branch on wall nodes
 };
 
 struct Scratch {
@@ -147,6 +148,7 @@ struct lbm_lattice {
   bool bound;
   int bx, by;
   int kernel;    // LBM_KERNEL_NODE, LBM_KERNEL_PAIR or LBM_KERNEL_BULK*
+  int wall_mode; // LBM_WALLS_AUTO / BRANCH / SELECT
   int sms;       // SM count of the bound device
   int pbx, pby;  // block shape of the pair kernel (pairs along x, rows)
   int device;

@@ -58,6 +58,12 @@ StepArgs make_args(const lbm_t *h, const void *fin, void *fout) {
   a.walls = h->flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z);
   a.z0 = 0;
   a.zn = h->nz;
+  // 16-bit storage is issue-bound: there the branch form's shorter common
+  // path wins once wall nodes are rare in every warp (long rows); FP32 is
+  // bandwidth-bound and the divergence-free select form is never slower
+  a.wall_select = h->wall_mode == LBM_WALLS_SELECT ||
+                  (h->wall_mode == LBM_WALLS_AUTO &&
+                   (h->storage == lbm::kF32 || h->nx < 256));
   for (int i = 0; i < lbm::Q; ++i) {
     a.lidc[i] = 0.0f;
     if ((h->flags & LBM_LID) && lbm::kEz[i] == -1)
@@ -251,6 +257,7 @@ int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
   h->bx = bx;
   h->by = by < 1 ? 1 : by;
   h->kernel = LBM_KERNEL_NODE;  // the pair kernel measured slower on GB300
+  h->wall_mode = LBM_WALLS_AUTO;
   h->pbx = 64;
   h->pby = ny < 4 ? ny : 4;
   h->device = -1;
@@ -338,6 +345,13 @@ int lbm_set_kernel(lbm_t *h, int variant) {
   if (variant == LBM_KERNEL_PAIR && h->storage == lbm::kF32)
     return fail(LBM_EINVAL, "the pair kernel needs 16-bit storage");
   h->kernel = variant;
+  return LBM_OK;
+}
+
+int lbm_set_wall_mode(lbm_t *h, int mode) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (mode < LBM_WALLS_AUTO || mode > LBM_WALLS_SELECT) return fail(LBM_EINVAL, "bad mode");
+  h->wall_mode = mode;
   return LBM_OK;
 }
 
@@ -536,8 +550,7 @@ int lbm_run_host(lbm_t *h, const float *u0_host, int n, float *rho_host,
   LBM_CUDA(cudaEventRecord(h->ev_start, h->stream), "event record");
   LBM_CUDA(cudaStreamWaitEvent(h->copy_in, h->ev_start, 0), "stream wait");
   LBM_CUDA(cudaStreamWaitEvent(h->copy_out, h->ev_start, 0), "stream wait");
-  // 1. copy u0 in by z slabs; each slab is initialised as soon as it arrives
-  for (int k = 0; k < S; ++k) {
+  auto copy_in_and_init = [&](int k) -> int {
     if (u0_host) {
       const size_t off = (size_t)zs[k] * nxy, len = (size_t)(zs[k + 1] - zs[k]) * nxy;
       for (int c = 0; c < 3; ++c)
@@ -553,13 +566,9 @@ int lbm_run_host(lbm_t *h, const float *u0_host, int n, float *rho_host,
     cudaError_t e = lbm::launch_init(h->storage, a, nullptr, u0_host ? u0d : nullptr, h->bx,
                                      h->by, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init kernel launch");
-  }
-  // 2. all but the last step over the whole lattice
-  rc = do_steps(h, n - 1, nullptr, nullptr);
-  if (rc) return rc;
-  // 3. the last step and the moments by z slabs; each slab is copied out as
-  //    soon as its moments are done
-  for (int k = 0; k < S; ++k) {
+    return LBM_OK;
+  };
+  auto last_step_and_copy_out = [&](int k) -> int {
     StepArgs a = make_args(h, h->f[h->cur], h->f[1 - h->cur]);
     a.z0 = zs[k];
     a.zn = zs[k + 1] - zs[k];
@@ -579,6 +588,42 @@ int lbm_run_host(lbm_t *h, const float *u0_host, int n, float *rho_host,
       LBM_CUDA(cudaMemcpyAsync(u_host + c * cells + off, ud + c * cells + off,
                                len * sizeof(float), cudaMemcpyDeviceToHost, h->copy_out),
                "u copy");
+    return LBM_OK;
+  };
+  if (n == 1 && S >= 3) {
+    // One step: slab k of the step needs slabs k - 1 .. k + 1 initialised
+    // (periodically), so slabs 1 .. S-2 step as soon as their upper
+    // neighbour has arrived, and their results leave while later slabs are
+    // still coming in; slabs S-1 and 0 (which wrap around) go last.
+    rc = copy_in_and_init(0);
+    if (rc) return rc;
+    rc = copy_in_and_init(1);
+    if (rc) return rc;
+    for (int k = 1; k <= S - 2; ++k) {
+      rc = copy_in_and_init(k + 1);
+      if (rc) return rc;
+      rc = last_step_and_copy_out(k);
+      if (rc) return rc;
+    }
+    rc = last_step_and_copy_out(S - 1);
+    if (rc) return rc;
+    rc = last_step_and_copy_out(0);
+    if (rc) return rc;
+  } else {
+    // 1. copy u0 in by z slabs; each slab is initialised as soon as it arrives
+    for (int k = 0; k < S; ++k) {
+      rc = copy_in_and_init(k);
+      if (rc) return rc;
+    }
+    // 2. all but the last step over the whole lattice
+    rc = do_steps(h, n - 1, nullptr, nullptr);
+    if (rc) return rc;
+    // 3. the last step and the moments by z slabs; each slab is copied out as
+    //    soon as its moments are done
+    for (int k = 0; k < S; ++k) {
+      rc = last_step_and_copy_out(k);
+      if (rc) return rc;
+    }
   }
   h->cur ^= 1;
   LBM_CUDA(cudaEventRecord(h->ev_done, h->copy_out), "event record");

@@ -36,7 +36,8 @@ __global__ void LBM_STEP_BOUNDS k_step(const StepArgs a) {
   if (x >= a.nx || y >= a.ny) return;
   step_node<S, WALLS, FORCE, MOM, false>(
       static_cast<const T *>(a.fin), static_cast<T *>(a.fout), a.nx, a.ny, a.nz, a.pitch,
-      a.plane, a.walls, a.lidc, a.omega, a.kf, a.force, a.rho, a.u, a.cells, x, y, z);
+      a.plane, a.walls, a.lidc, a.omega, a.kf, a.force, a.rho, a.u, a.cells, x, y, z,
+      a.wall_select != 0);
 }
 
 template <int S>

@@ -104,6 +104,24 @@ __device__ __forceinline__ void gather_walled(const typename Store<S>::T *__rest
   });
 }
 
+// Halfway bounce-back applied after a plain periodic gather, only on nodes
+// that touch a walled face (a branch; cheaper than gather_walled when wall
+// nodes are a small fraction of each warp's nodes, i.e. on long rows).
+template <int S, bool L2ONLY = false>
+__device__ __forceinline__ void bounce_fixup(const typename Store<S>::T *__restrict__ fin,
+                                             uint32_t plane, const NodeIdx &n,
+                                             const float (&lidc)[Q], float (&d)[Q]) {
+  if (!on_wall(n)) return;
+  static_for<1, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if (bounces<i>(n)) {
+      float v = load_f<S, L2ONLY>(fin + (size_t)kOpp_v<i> * plane + n.c);
+      if constexpr (kEz[i] == -1) v += n.z1 ? lidc[i] : 0.0f;
+      d[i] = v;
+    }
+  });
+}
+
 // One fused update of node (x, y, z) (Alg. 3): pull gather, boundary rule,
 // moments, equilibrium, BGK (+ Guo force) collide, aligned store of the 19
 // post-collision values at the node; optionally also rho and u into dense
@@ -114,13 +132,19 @@ __device__ __forceinline__ void step_node(
     int nx, int ny, int nz, int pitch, uint32_t plane, uint32_t walls,
     const float (&lidc)[Q], float omega, float kf, const float *__restrict__ force,
     float *__restrict__ rho_out, float *__restrict__ u_out, uint32_t cells, int x, int y,
-    int z) {
+    int z, bool wall_select = true) {
   const NodeIdx n = node_index(nx, ny, nz, pitch, walls, x, y, z);
   float d[Q];
-  if constexpr (WALLS)
-    gather_walled<S, L2ONLY>(fin, plane, n, lidc, d);
-  else
+  if constexpr (WALLS) {
+    if (wall_select) {
+      gather_walled<S, L2ONLY>(fin, plane, n, lidc, d);
+    } else {
+      gather<S, L2ONLY>(fin, plane, n, d);
+      bounce_fixup<S, L2ONLY>(fin, plane, n, lidc, d);
+    }
+  } else {
     gather<S, L2ONLY>(fin, plane, n, d);
+  }
   const uint32_t dc = ((uint32_t)z * ny + y) * nx + x;
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
   if constexpr (FORCE) {

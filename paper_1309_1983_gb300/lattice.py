@@ -120,6 +120,12 @@ class Lattice:
              "bulk": capi.LBM_KERNEL_BULK, "bulk1": capi.LBM_KERNEL_BULK1}[variant]
         capi.call("lbm_set_kernel", self._h, v)
 
+    def set_wall_mode(self, mode):
+        """"auto", "branch" or "select" (see lbm_set_wall_mode)."""
+        v = {"auto": capi.LBM_WALLS_AUTO, "branch": capi.LBM_WALLS_BRANCH,
+             "select": capi.LBM_WALLS_SELECT}[mode]
+        capi.call("lbm_set_wall_mode", self._h, v)
+
     def set_pair_block(self, bxp, by):
         capi.call("lbm_set_pair_block", self._h, int(bxp), int(by))
 

@@ -223,18 +223,26 @@ def test_step_to_matches_step():
     assert torch.equal(out, cur2)
 
 
-def test_run_host_matches_device_path():
-    n = 24
-    u0 = torch.from_numpy(W.fourier_modes(n, n, n, seed=4, amp=0.02)).float()
-    L = _lat(n, n, n, 0.8)
-    rho_h = torch.empty((n, n, n)).pin_memory()
-    u_h = torch.empty((3, n, n, n)).pin_memory()
-    L.run_host(u0.pin_memory(), 7, rho_h, u_h)
-    L2 = _lat(n, n, n, 0.8)
+@pytest.mark.parametrize("steps", [1, 7])
+@pytest.mark.parametrize("shape", [(24, 24, 24), (19, 7, 2), (33, 5, 17)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_run_host_matches_device_path(steps, shape):
+    """The end-to-end host call (slab-pipelined transfers; single steps
+    interleave the inbound copies, the slab steps and the outbound copies)
+    gives exactly the device path's result."""
+    nx, ny, nz = shape
+    u0 = torch.from_numpy(W.fourier_modes(nx, ny, nz, seed=4, kmax=2.0, amp=0.02)).float()
+    L = _lat(nx, ny, nz, 0.8, (0, 1, 1), (0.03, 0, 0))
+    rho_h = torch.empty((nz, ny, nx)).pin_memory()
+    u_h = torch.empty((3, nz, ny, nx)).pin_memory()
+    L.run_host(u0.pin_memory(), steps, rho_h, u_h)
+    L2 = _lat(nx, ny, nz, 0.8, (0, 1, 1), (0.03, 0, 0))
     L2.init_equilibrium(u=u0.cuda())
-    L2.step(7)
+    L2.step(steps)
     rho, u = L2.moments()
     assert torch.equal(rho.cpu(), rho_h) and torch.equal(u.cpu(), u_h)
+    # the state left behind is the device path's state too
+    np.testing.assert_array_equal(L.get_f(), L2.get_f())
 
 
 def test_nonfinite_density_is_reported():
@@ -335,3 +343,20 @@ def test_push_iteration_tracks_streamed_pull_states(geom, force):
         a, b = b, a
     ref = O.stream(OL, O.run(OL, f0, 4, F))
     assert np.abs(L.buffer_to_numpy(a) - ref).max() <= ATOL_F
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("shape", [(37, 11, 9), (260, 5, 4)], ids=lambda s: "x".join(map(str, s)))
+def test_wall_modes_agree(storage, shape):
+    """Branching on wall nodes and selecting addresses for every node give
+    the same bits (cavity with lid, walls on every axis)."""
+    nx, ny, nz = shape
+    outs = []
+    for mode in ("branch", "select", "auto"):
+        L = _lat(nx, ny, nz, 0.6, (1, 1, 1), (0.05, 0.01, 0.0), storage=storage)
+        L.set_wall_mode(mode)
+        L.init_equilibrium()
+        L.step(6)
+        outs.append(L.get_f())
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
