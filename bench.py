@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--n", type=int, default=N_DEFAULT, help="lattice edge (cube)")
     p.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     p.add_argument("--extras", default="all",
-                   help="comma list of secondary workloads: storage,streaming,adjoint,batched "
+                   help="comma list of secondary workloads: storage,streaming,adjoint,batched,sweep "
                         "(or all)")
     p.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                    help="storage of the main timed workload (profiling runs)")
@@ -270,6 +270,47 @@ def extra_workloads(torch, n, steps=100, warmup=10):
     return out
 
 
+def size_sweep(torch, sizes=(64, 128, 256), steps=1000):
+    """The periodic shear-wave sweep: tau = 0.8, u_x = 0.01 sin(2 pi z/N)
+    from equilibrium, FP32, `steps` single-update launches per size timed
+    with CUDA events; the wave amplitude (projection of u_x on the initial
+    sine) is sampled every steps/10 updates in an untimed second pass and
+    its fitted decay rate compared with nu k^2 (Sec. 5 physics check at every
+    size). 64^3 (20 MB per copy) stays resident in the 129 MB L2."""
+    import numpy as np
+    from paper_1309_1983_gb300.lattice import Lattice
+    from paper_1309_1983_gb300 import workloads as W
+    out = {}
+    nu = (TAU - 0.5) / 3.0
+    for n in sizes:
+        L = Lattice(n, n, n, TAU)
+        u0 = torch.from_numpy(W.shear_wave(n, n, n, AMP)).float().cuda()
+        L.init_equilibrium(u=u0)
+        L.step(10)
+        ms, per = timed_steps(L, steps, torch)
+        L.init_equilibrium(u=u0)
+        sn = torch.sin(2 * np.pi * torch.arange(n, dtype=torch.float64) / n).cuda()
+        t, A = [], []
+        for k in range(11):
+            _, u = L.moments()
+            A.append(float((u[0].double().mean(dim=(1, 2)) * sn).sum() * 2 / n))
+            t.append(k * (steps // 10))
+            if k < 10:
+                L.step(steps // 10)
+        rate = -np.polyfit(np.array(t, dtype=np.float64), np.log(np.array(A)), 1)[0]
+        kk = 2 * np.pi / n
+        mlups = n ** 3 * steps / (ms / 1e3) / 1e6
+        out[f"periodic_{n}"] = {
+            "mlups": round(mlups, 1), "gbs": round(mlups * 152 / 1e3, 1),
+            "best_step_mlups": round(n ** 3 / (min(per) / 1e3) / 1e6, 1),
+            "decay_rate_rel_err": float(rate / (nu * kk * kk) - 1.0),
+            "l2_resident": 152 * n ** 3 < 129e6}
+        L.close()
+        del L, u0
+        torch.cuda.empty_cache()
+    return out
+
+
 def streaming_ablation(torch, n, steps=50):
     """Sec. 4.3 redone on this GPU: streaming alone as an unshifted copy, a
     gather (misaligned reads) and a scatter (misaligned writes), and the full
@@ -349,50 +390,54 @@ def batch_workload(torch, steps=2000):
     from paper_1309_1983_gb300.lattice import Lattice
     G = W.batch_geometry(64, seed=3)
     B = Batch(G.dims, G.tau, G.lid_u)
-    table = {}
-    tiling = autotune.tune_batch(B, steps=50, cache_path=None, table=table)
+    tiling = autotune.tune_batch(B, steps=50, cache_path=None)
+    s = B.stream
+
+    def dev_ms(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fn()
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
     B.init_rest()
-    B.step(10)
-    t0 = time.perf_counter()
-    B.step(steps)
-    dt = time.perf_counter() - t0
+    B.step(steps)  # untimed: capture the graphs of a `steps`-step launch
+    B.step(steps)  # from either buffer parity
+    B.init_rest()
+    ms = dev_ms(lambda: B.step(steps))  # replayed from a captured graph
     cells = int(G.dims.prod(axis=1).sum())
     info = B.info()
     # the same steps as one ordinary launch per step over the tile table
     B.step_launches(5)
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    B.step_launches(200)
-    torch.cuda.synchronize()
-    dt_launch = time.perf_counter() - t2
+    ms_launch = dev_ms(lambda: B.step_launches(200))
     B.close()
     lats = []
     for d in range(64):
         nx, ny, nz = (int(v) for v in G.dims[d])
         L = Lattice(nx, ny, nz, float(G.tau[d]), walls=(True, True, True),
-                    lid=(float(G.lid_u[d]), 0.0, 0.0))
+                    lid=(float(G.lid_u[d]), 0.0, 0.0), stream=s)
         L.init_equilibrium()
         lats.append(L)
     sep_steps = 200
     for L in lats:
         L.step(2)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    for _ in range(sep_steps):
-        for L in lats:
-            L.step(1)
-    torch.cuda.synchronize()
-    dt_sep = time.perf_counter() - t1
+
+    def separate():
+        for _ in range(sep_steps):
+            for L in lats:
+                L.step(1)
+    ms_sep = dev_ms(separate)
     for L in lats:
         L.close()
     del lats
     torch.cuda.empty_cache()
     adj = batch_adjoint_workload(torch, G, steps)
     return {"domains": 64, "cells": cells, "steps": steps, "forward_plus_adjoint": adj,
-            "persistent_mlups": round(cells * steps / dt / 1e6, 1),
-            "tile_launch_per_step_mlups": round(cells * 200 / dt_launch / 1e6, 1),
-            "tuner_ms_per_step": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in table.items()},
-            "separate_launches_mlups": round(cells * sep_steps / dt_sep / 1e6, 1),
+            "persistent_mlups": round(cells * steps / ms / 1e3, 1),
+            "tile_launch_per_step_mlups": round(cells * 200 / ms_launch / 1e3, 1),
+            "tuned_ms_per_step": round(tiling[2], 4),
+            "separate_launches_mlups": round(cells * sep_steps / ms_sep / 1e3, 1),
             "tiling": {"threads": tiling[0], "blocks_per_sm": tiling[1]},
             "grid": info["grid"], "graph": info["graph"]}
 
@@ -514,8 +559,10 @@ def run_ours(args):
         del L, u0
         torch.cuda.empty_cache()
         want = set(args.extras.split(",")) if args.extras != "all" else {
-            "storage", "streaming", "adjoint", "batched"}
+            "storage", "streaming", "adjoint", "batched", "sweep"}
         extras = {}
+        if "sweep" in want:
+            extras["sweep"] = size_sweep(torch)
         if "storage" in want:
             extras.update(extra_workloads(torch, n))
         if "streaming" in want:

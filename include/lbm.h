@@ -158,6 +158,22 @@ int lbm_set_wall_mode(lbm_t *h, int mode);
  * `by` rows, bxp * by <= 256. Default: 64 x 4 (or fewer rows for small ny). */
 int lbm_set_pair_block(lbm_t *h, int bxp, int by);
 
+/* Launch-shape autotuner (no counterpart in the paper, which fixed its block
+ * shape by hand, Sec. 6). Times every x-dominant block shape (32..256 threads
+ * along x, at most the rounded-up row; 1..8 rows; 64..256 threads) of the
+ * current kernel variant (the pair block for LBM_KERNEL_PAIR) over `steps`
+ * calls of lbm_step after the same number untimed, with CUDA events on the
+ * bound stream, and applies the fastest. This ADVANCES THE STATE by all the
+ * steps it runs: tune before initialising the state you want.
+ * cache_path: NULL for no cache; else a text file of "key<TAB>a<TAB>b<TAB>ms"
+ * lines, key = GPU name and SM count, lattice size, flags, kernel variant and
+ * wall mode. A hit applies the cached shape without running anything; a miss
+ * tunes and rewrites the file with the new line (temporary file + rename).
+ * Outputs (may be NULL): the shape and its time per step in ms.
+ * Errors: LBM_EINVAL (NULL handle, steps outside [1, 100000], cache not
+ * writable), LBM_EUNBOUND, LBM_ECUDA from a step or the timing. */
+int lbm_autotune(lbm_t *h, const char *cache_path, int steps, int *bx, int *by, float *ms);
+
 /* Device pointers of the current state and of the other (scratch) buffer. */
 int lbm_current(const lbm_t *h, void **f_cur, void **f_other);
 
@@ -278,7 +294,10 @@ int lbm_adjoint_seed(lbm_t *h, const void *f_T, const float *u_target,
  * it). If grad_force is non-NULL, (dC/dF)^T lambda^{n+1} is ADDED into it
  * (the gradient at the bound force, or at F = 0 without LBM_FORCE).
  * lambda_in and lambda_out must not overlap; every element of lambda_out is
- * written exactly once (the transposed pull is a permutation). */
+ * written exactly once (the transposed pull is a permutation). Launch: 64 x 2
+ * blocks (32 x 4 for rows of 32 nodes or fewer); walls by address selection when
+ * the wall mode is LBM_WALLS_SELECT, or LBM_WALLS_AUTO with rows shorter than
+ * 256 nodes, else by a branch on wall nodes. */
 int lbm_adjoint_step(lbm_t *h, const void *f_n, const float *lambda_in,
                      float *lambda_out, float *grad_force);
 
@@ -321,6 +340,17 @@ int lbm_batch_bind(lbm_batch_t *b, void *f_a, void *f_b, void *stream);
  * multiple of 32); blocks_per_sm caps the persistent grid (0 = occupancy
  * limit). Chosen by the autotuner. */
 int lbm_batch_set_tiling(lbm_batch_t *b, int threads, int blocks_per_sm);
+
+/* Tiling autotuner of the persistent batched step: times threads in
+ * {64, 128, 256} x blocks_per_sm in {0, 2, 4, 6, 8}, each over one
+ * lbm_batch_step of `steps` steps (rounded up to even) after one untimed call
+ * that also captures its graph, and applies the fastest. Advances the state.
+ * The cache works as for lbm_autotune, keyed by GPU, domain count, a hash of
+ * the domain sizes and walls, and the flags. Outputs may be NULL. Errors:
+ * LBM_EINVAL (bad steps, cache not writable), LBM_EUNBOUND, LBM_ECUDA,
+ * LBM_ETIMEOUT from a step. */
+int lbm_batch_autotune(lbm_batch_t *b, const char *cache_path, int steps, int *threads,
+                       int *blocks_per_sm, float *ms);
 
 /* Wall-clock limit of one grid-barrier wait, (0, 60] seconds (default 1). */
 int lbm_batch_set_timeout(lbm_batch_t *b, double seconds);

@@ -81,6 +81,7 @@ _SIGNATURES = {
     "lbm_set_kernel": [_vp, _i],
     "lbm_set_pair_block": [_vp, _i, _i],
     "lbm_set_wall_mode": [_vp, _i],
+    "lbm_autotune": [_vp, ctypes.c_char_p, _i, _vp, _vp, _vp],
     "lbm_current": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "lbm_init_equilibrium": [_vp, _vp, _vp],
     "lbm_step": [_vp, _i],
@@ -103,6 +104,7 @@ _SIGNATURES = {
     "lbm_batch_layout": [_vp, _vp, _vp, _vp, _vp],
     "lbm_batch_bind": [_vp, _vp, _vp, _vp],
     "lbm_batch_set_tiling": [_vp, _i, _i],
+    "lbm_batch_autotune": [_vp, ctypes.c_char_p, _i, _vp, _vp, _vp],
     "lbm_batch_set_timeout": [_vp, ctypes.c_double],
     "lbm_batch_inject_barrier_fault": [_vp, _i],
     "lbm_batch_use_graph": [_vp, _i],

@@ -68,18 +68,24 @@ __device__ __forceinline__ void mat_vec(const float (&L2)[6], float vx, float vy
 
 // One reverse step at node (x, y, z): recompute g = P f^n there, form
 // mu = J_C(g)^T lambda^{n+1}(x), scatter it by P^T into lambda_out, and add
-// the force cotangent into gF (GRADF).
-template <bool FORCE, bool GRADF>
+// the force cotangent into gF (GRADF). WALLS = false compiles the periodic
+// form only; with WALLS the gather and the scatter apply the bounce-back rule
+// either by per-direction address selection on every node (wall_select) or
+// only on nodes that touch a walled face (a branch, cheaper on long rows).
+template <bool WALLS, bool FORCE, bool GRADF>
 __device__ __forceinline__ void adjoint_node(
     const float *__restrict__ fn, const float *__restrict__ lam_in,
     float *__restrict__ lam_out, const float *__restrict__ force, float *__restrict__ gF,
     int nx, int ny, int nz, int pitch, uint32_t plane, uint32_t walls,
-    const float (&lidc)[Q], float omega, float kf, uint32_t cells, int x, int y, int z) {
-  const NodeIdx n = node_index(nx, ny, nz, pitch, walls, x, y, z);
+    const float (&lidc)[Q], float omega, float kf, uint32_t cells, int x, int y, int z,
+    bool wall_select = true) {
+  const NodeIdx n = node_index(nx, ny, nz, pitch, WALLS ? walls : 0u, x, y, z);
+  // bounce-back handled per direction on this node (uniform when selecting)
+  const bool sel = WALLS && (wall_select || on_wall(n));
 
   // recompute the post-streaming state g = P f^n of the forward step
   float d[Q];
-  if (walls)
+  if (sel)
     gather_walled<0>(fn, plane, n, lidc, d);
   else
     gather<0>(fn, plane, n, d);
@@ -135,17 +141,25 @@ __device__ __forceinline__ void adjoint_node(
     gF[2 * (size_t)cells + dc] += fmaf(kf, sz, 0.5f * Bz);
   }
 
-  // mu_j = (1 - omega) lambda_j + A + B . e_j, scattered by P^T
-  const bool wall = walls && on_wall(n);
+  // mu_j = (1 - omega) lambda_j + A + B . e_j, in place, then scattered by P^T
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr float cx = (float)kEx[i], cy = (float)kEy[i], cz = (float)kEz[i];
-    const float mu = fmaf(keep, lam[i], A + (cx * Bx + cy * By + cz * Bz));
-    if (wall && bounces<i>(n))
-      lam_out[(size_t)kOpp_v<i> * plane + n.c] = mu;
-    else
-      lam_out[(size_t)i * plane + source_of<i>(n)] = mu;
+    lam[i] = fmaf(keep, lam[i], A + (cx * Bx + cy * By + cz * Bz));
   });
+  if (sel) {
+    static_for<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const size_t idx = bounces<i>(n) ? (size_t)kOpp_v<i> * plane + n.c
+                                       : (size_t)i * plane + source_of<i>(n);
+      lam_out[idx] = lam[i];
+    });
+  } else {
+    static_for<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      lam_out[(size_t)i * plane + source_of<i>(n)] = lam[i];
+    });
+  }
 }
 
 // Loss seed at node (x, y, z) of a stored state f_T:

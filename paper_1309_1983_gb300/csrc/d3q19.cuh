@@ -139,12 +139,20 @@ __device__ __forceinline__ void collide(float (&d)[Q], float omega, float kf,
   const float usq15 = 1.5f * fmaf(ux, ux, fmaf(uy, uy, uz * uz));
   float uF = 0.0f;
   if constexpr (FORCE) uF = fmaf(ux, Fx, fmaf(uy, Fy, uz * Fz));
+  // f*_i = (1 - omega) g_i + omega f^eq_i, with omega folded into the
+  // weights. The velocity is pre-scaled by sqrt(9/2) so that one FMA gives
+  // 4.5 (e.u)^2 - 1.5 u^2; the odd part 3 w rho (e.u) then takes one multiply
+  // by a per-weight-class factor.
+  constexpr float kS = 2.12132034355964257f;  // sqrt(9/2)
+  const float keep = 1.0f - omega;
+  const float vx = kS * ux, vy = kS * uy, vz = kS * uz;
+  const float owA = omega * weight(1), owB = omega * weight(7);
+  const float roA = ((3.0f / kS) * rho) * owA, roB = ((3.0f / kS) * rho) * owB;
 
   // rest direction
   {
     constexpr float w = weight(0);
-    const float feq = w * fmaf(-rho, usq15, dr);
-    float v = fmaf(omega, feq - d[0], d[0]);
+    float v = fmaf(keep, d[0], (omega * w) * fmaf(-rho, usq15, dr));
     if constexpr (FORCE) v = fmaf(kf, w * (-3.0f * uF), v);
     d[0] = v;
   }
@@ -153,14 +161,15 @@ __device__ __forceinline__ void collide(float (&d)[Q], float omega, float kf,
     constexpr int j = i + 1;                        // its opposite
     constexpr float w = weight(i);
     constexpr float cx = (float)kEx[i], cy = (float)kEy[i], cz = (float)kEz[i];
-    const float eu = cx * ux + cy * uy + cz * uz;  // folds to adds/subs
-    const float even = w * fmaf(rho, fmaf(4.5f * eu, eu, -usq15), dr);
-    const float odd = (3.0f * w) * rho * eu;
-    float vi = fmaf(omega, (even + odd) - d[i], d[i]);
-    float vj = fmaf(omega, (even - odd) - d[j], d[j]);
+    const float ow = i < 7 ? owA : owB, ro = i < 7 ? roA : roB;
+    const float es = cx * vx + cy * vy + cz * vz;  // sqrt(9/2) e.u; folds to adds/subs
+    const float even = ow * fmaf(rho, fmaf(es, es, -usq15), dr);
+    const float odd = ro * es;
+    float vi = fmaf(keep, d[i], even + odd);
+    float vj = fmaf(keep, d[j], even - odd);
     if constexpr (FORCE) {
       const float eF = cx * Fx + cy * Fy + cz * Fz;
-      const float sEven = w * fmaf(9.0f * eu, eF, -3.0f * uF);
+      const float sEven = w * fmaf((9.0f / kS) * es, eF, -3.0f * uF);
       const float sOdd = (3.0f * w) * eF;
       vi = fmaf(kf, sEven + sOdd, vi);
       vj = fmaf(kf, sEven - sOdd, vj);

@@ -22,16 +22,17 @@ struct AdjArgs {
 #define LBM_ADJ_MIN_BLOCKS 3
 #endif
 
-template <bool FORCE, bool GRADF>
+template <bool WALLS, bool FORCE, bool GRADF>
 __global__ void __launch_bounds__(256, LBM_ADJ_MIN_BLOCKS) k_adjoint_step(const AdjArgs a) {
   const StepArgs &g = a.g;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= g.nx || y >= g.ny) return;
-  adjoint_node<FORCE, GRADF>(static_cast<const float *>(g.fin), a.lam_in, a.lam_out, g.force,
-                             a.grad_force, g.nx, g.ny, g.nz, g.pitch, g.plane, g.walls, g.lidc,
-                             g.omega, g.kf, g.cells, x, y, z);
+  adjoint_node<WALLS, FORCE, GRADF>(static_cast<const float *>(g.fin), a.lam_in, a.lam_out,
+                                    g.force, a.grad_force, g.nx, g.ny, g.nz, g.pitch, g.plane,
+                                    g.walls, g.lidc, g.omega, g.kf, g.cells, x, y, z,
+                                    g.wall_select != 0);
 }
 
 // Seed over all nodes (grid stride), FP64 loss partials per block.
@@ -75,11 +76,17 @@ cudaError_t launch_adjoint_step(const StepArgs &g, const float *lam_in,
   a.u_target = nullptr;
   a.partials = nullptr;
   const dim3 grid((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz), blk(bx, by, 1);
-  const bool F = g.force != nullptr, G = grad_force != nullptr;
-  if (F && G) k_adjoint_step<true, true><<<grid, blk, 0, s>>>(a);
-  else if (F) k_adjoint_step<true, false><<<grid, blk, 0, s>>>(a);
-  else if (G) k_adjoint_step<false, true><<<grid, blk, 0, s>>>(a);
-  else k_adjoint_step<false, false><<<grid, blk, 0, s>>>(a);
+  const int v = (g.walls ? 4 : 0) | (g.force ? 2 : 0) | (grad_force ? 1 : 0);
+  switch (v) {
+    case 0: k_adjoint_step<false, false, false><<<grid, blk, 0, s>>>(a); break;
+    case 1: k_adjoint_step<false, false, true><<<grid, blk, 0, s>>>(a); break;
+    case 2: k_adjoint_step<false, true, false><<<grid, blk, 0, s>>>(a); break;
+    case 3: k_adjoint_step<false, true, true><<<grid, blk, 0, s>>>(a); break;
+    case 4: k_adjoint_step<true, false, false><<<grid, blk, 0, s>>>(a); break;
+    case 5: k_adjoint_step<true, false, true><<<grid, blk, 0, s>>>(a); break;
+    case 6: k_adjoint_step<true, true, false><<<grid, blk, 0, s>>>(a); break;
+    default: k_adjoint_step<true, true, true><<<grid, blk, 0, s>>>(a); break;
+  }
   return cudaGetLastError();
 }
 

@@ -214,10 +214,11 @@ __global__ void __launch_bounds__(256, 3)
   if (k >= D.cells) return;
   int x, y, z;
   decode(D, k, x, y, z);
-  adjoint_node<false, GRADF>(fn + D.foff, lam_in + D.foff, lam_out + D.foff, nullptr,
-                             GRADF ? gF + 3 * (size_t)D.coff : nullptr, D.nx, D.ny, D.nz,
-                             D.pitch, D.plane, D.walls, D.lidc, D.omega, D.kf, D.cells, x, y,
-                             z);
+  // small domains: wall nodes in most warps, so bounce-back by address selection
+  adjoint_node<true, false, GRADF>(fn + D.foff, lam_in + D.foff, lam_out + D.foff, nullptr,
+                                   GRADF ? gF + 3 * (size_t)D.coff : nullptr, D.nx, D.ny, D.nz,
+                                   D.pitch, D.plane, D.walls, D.lidc, D.omega, D.kf, D.cells,
+                                   x, y, z, true);
 }
 
 // Seed per node, FP64 loss partial per tile (block) into partials[tile].

@@ -13,6 +13,7 @@
 
 #include "d3q19.cuh"
 #include "internal.h"
+#include "tune.h"
 
 using lbm::BatchArgs;
 using lbm::BatchDom;
@@ -493,6 +494,69 @@ int lbm_batch_adjoint_u0(lbm_batch_t *b, const float *lambda0, const float *u0,
   if (!lambda0 || !grad_u0) return bfail(LBM_EINVAL, "NULL buffer");
   BCUDA(lbm::launch_batch_adjoint_u0(make_args(b), lambda0, u0, grad_u0, b->threads, b->stream),
         "batch u0 gradient launch");
+  return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch_t *b, const char *cache_path, int steps, int *threads_out,
+                       int *blocks_per_sm_out, float *ms_out) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (steps < 1 || steps > 100000) return bfail(LBM_EINVAL, "steps in [1, 100000]");
+  steps += steps & 1;  // even: the timed call replays the graph the untimed one captured
+  // key: GPU, the domain list (FNV-1a over dims and walls) and the flags
+  uint64_t hsh = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) {
+    for (int k = 0; k < 8; ++k) {
+      hsh ^= (v >> (8 * k)) & 0xffu;
+      hsh *= 1099511628211ull;
+    }
+  };
+  for (const BatchDom &D : b->doms) {
+    mix((uint64_t)D.nx);
+    mix((uint64_t)D.ny);
+    mix((uint64_t)D.nz);
+    mix((uint64_t)D.walls);
+  }
+  char geo[96];
+  snprintf(geo, sizeof geo, "batch/%d/%016llx/flags%u", b->ndom, (unsigned long long)hsh,
+           b->flags);
+  const std::string key = lbm::device_key(b->device) + "/" + geo;
+  int t = 0, bps = 0;
+  float best_ms = 0.f;
+  if (lbm::tune_cache_lookup(cache_path, key, &t, &bps, &best_ms) &&
+      lbm_batch_set_tiling(b, t, bps) == LBM_OK) {
+    if (threads_out) *threads_out = t;
+    if (blocks_per_sm_out) *blocks_per_sm_out = bps;
+    if (ms_out) *ms_out = best_ms;
+    return LBM_OK;
+  }
+  // tile sizes x resident blocks per SM (0 = as many as fit) of the
+  // persistent launch; the untimed first call also captures its graph
+  static const int kThreads[] = {64, 128, 256};
+  static const int kBps[] = {0, 2, 4, 6, 8};
+  int best_t = 0, best_b = 0;
+  for (int tt : kThreads) {
+    for (int bb : kBps) {
+      rc = lbm_batch_set_tiling(b, tt, bb);
+      if (rc) return rc;
+      float ms = 0.f;
+      rc = lbm::time_calls(b->stream, 1, [&]() { return lbm_batch_step(b, steps); }, &ms);
+      if (rc) return rc;
+      ms /= steps;
+      if (!best_t || ms < best_ms) {
+        best_t = tt;
+        best_b = bb;
+        best_ms = ms;
+      }
+    }
+  }
+  rc = lbm_batch_set_tiling(b, best_t, best_b);
+  if (rc) return rc;
+  if (lbm::tune_cache_store(cache_path, key, best_t, best_b, best_ms))
+    return bfail(LBM_EINVAL, "autotune cache not writable");
+  if (threads_out) *threads_out = best_t;
+  if (blocks_per_sm_out) *blocks_per_sm_out = best_b;
+  if (ms_out) *ms_out = best_ms;
   return LBM_OK;
 }
 

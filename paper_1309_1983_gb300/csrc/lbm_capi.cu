@@ -659,10 +659,14 @@ int lbm_adjoint_step(lbm_t *h, const void *f_n, const float *lambda_in,
   if (!f_n || !lambda_in || !lambda_out || lambda_in == lambda_out)
     return fail(LBM_EINVAL, "bad buffers");
   StepArgs g = make_args(h, f_n, nullptr);
-  // single-row blocks measured fastest for the adjoint's three node streams
-  const int aby = h->bx >= 128 ? 1 : h->by;
-  cudaError_t e = lbm::launch_adjoint_step(g, lambda_in, lambda_out, grad_force,
-                                           h->bx, aby, h->stream);
+  // The adjoint issues ~1.7x the forward's instructions per node: the branch
+  // form (fewer instructions off the walls) wins once rows are long, and
+  // 64 x 2 blocks measured best for both periodic and walled lattices.
+  g.wall_select = h->wall_mode == LBM_WALLS_SELECT ||
+                  (h->wall_mode == LBM_WALLS_AUTO && h->nx < 256);
+  const int abx = h->nx <= 32 ? 32 : 64;
+  cudaError_t e = lbm::launch_adjoint_step(g, lambda_in, lambda_out, grad_force, abx,
+                                           128 / abx, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint step launch");
   return LBM_OK;
 }

@@ -1,0 +1,102 @@
+"""Lid-driven cavity validation by self-convergence (Sec. 5).
+
+The paper checks its solver on the cubic lid-driven cavity at Re = 100, 400
+and 1000 by comparing centre-line velocity profiles with published data.
+That data is not available here, so the check is the convergence itself:
+the same cavity at successive resolutions N (Eq. 8 with L = N gives
+tau = 1/2 + 3 N U / Re), each run to a steady state, and the profile
+u_x(z)/U on the vertical centre line compared on the coarsest lattice's
+node positions. Halfway bounce-back makes the scheme second order, so the
+change between successive resolutions should shrink by about 4 per doubling.
+
+Command line (writes one JSON object):
+
+    python -m paper_1309_1983_gb300.validation --re 400 --sizes 48,96,192 --u 0.1
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import perfmodel as PM
+
+
+def tau_for(N: int, U: float, Re: float) -> float:
+    """Relaxation time giving Reynolds number Re on an N^3 cavity (Eq. 8)."""
+    return 0.5 + 3.0 * N * U / Re
+
+
+def centre_profile(N: int, Re: float, U: float = 0.05, tol: float = 2e-5,
+                   max_chunks: int = 200, storage: str = "f32"):
+    """Run an N^3 cavity from rest to a steady state and return
+    (z, u_x(z)/U, steps, converged): z the node centres in units of the
+    edge (halfway walls at 0 and 1), the profile on the vertical centre line
+    (mean of the central one or two columns in x and y). Steady means the
+    profile moved by less than ``tol`` (in units of U) over one chunk of
+    max(1000, 5 N / U) steps."""
+    import torch
+    from .lattice import Lattice
+    tau = tau_for(N, U, Re)
+    assert abs(PM.reynolds(U, tau, N) - Re) < 1e-9 * Re
+    L = Lattice(N, N, N, tau, walls=(True, True, True), lid=(U, 0.0, 0.0), storage=storage)
+    try:
+        L.init_equilibrium()
+        chunk = max(1000, int(5 * N / U))
+        c = [N // 2 - 1, N // 2] if N % 2 == 0 else [N // 2]
+        prev, steps, converged = None, 0, False
+        for _ in range(max_chunks):
+            L.step(chunk)
+            steps += chunk
+            _, u = L.moments()
+            prof = u[0][:, c][:, :, c].double().mean(dim=(1, 2)).cpu().numpy() / U
+            if not np.isfinite(prof).all():
+                break
+            if prev is not None and np.abs(prof - prev).max() < tol:
+                converged = True
+                break
+            prev = prof
+        torch.cuda.synchronize()
+    finally:
+        L.close()
+    z = (np.arange(N) + 0.5) / N
+    return z, prof, steps, converged
+
+
+def self_convergence(Re: float, sizes=(24, 48, 96), U: float = 0.05, **kw):
+    """Profiles at each size, interpolated to the coarsest lattice's nodes,
+    and the successive maximum differences d_k = max |p_{k+1} - p_k| with
+    their ratios (about 4 at second order when the sizes double)."""
+    runs = [centre_profile(N, Re, U, **kw) for N in sizes]
+    zc = runs[0][0]
+    on_coarse = [np.interp(zc, z, p) for z, p, _, _ in runs]
+    diffs = [float(np.abs(on_coarse[k + 1] - on_coarse[k]).max())
+             for k in range(len(sizes) - 1)]
+    ratios = [diffs[k] / diffs[k + 1] for k in range(len(diffs) - 1)]
+    return {"Re": Re, "U": U, "sizes": list(sizes),
+            "tau": [tau_for(N, U, Re) for N in sizes],
+            "steps": [r[2] for r in runs], "converged": [r[3] for r in runs],
+            "diffs": diffs, "ratios": ratios,
+            "z": zc.tolist(), "profiles_on_coarse": [p.tolist() for p in on_coarse]}
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--re", type=float, required=True)
+    p.add_argument("--sizes", default="24,48,96")
+    p.add_argument("--u", type=float, default=0.05)
+    p.add_argument("--tol", type=float, default=2e-5)
+    a = p.parse_args(argv)
+    t0 = time.time()
+    out = self_convergence(a.re, tuple(int(s) for s in a.sizes.split(",")), a.u, tol=a.tol)
+    out["seconds"] = round(time.time() - t0, 1)
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

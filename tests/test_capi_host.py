@@ -79,8 +79,14 @@ def test_unbound_handle_is_reported(lib):
         assert lib.lbm_set_block(h, 48, 1) == capi.LBM_EINVAL
         assert lib.lbm_set_block(h, 128, 4) == capi.LBM_EINVAL
         assert lib.lbm_set_block(h, 64, 4) == 0
+        assert lib.lbm_autotune(h, None, 5, None, None, None) == capi.LBM_EUNBOUND
     finally:
         lib.lbm_destroy(h)
+
+
+def test_autotune_rejects_bad_arguments(lib):
+    assert lib.lbm_autotune(None, None, 5, None, None, None) == capi.LBM_EINVAL
+    assert lib.lbm_batch_autotune(None, None, 5, None, None, None) == capi.LBM_EINVAL
 
 
 def test_lid_needs_lid_flag(lib):

@@ -79,13 +79,18 @@ def _random_f(OL, seed):
     return f * (1.0 + W.noise(f.shape, seed + 2, 0.1))
 
 
+@pytest.mark.parametrize("mode", ["auto", "branch", "select"])
 @pytest.mark.parametrize("geom", sorted(GEOMS))
 @pytest.mark.parametrize("shape", [(37, 6, 5), (8, 8, 8), (1, 5, 7)], ids=lambda s: "x".join(map(str, s)))
-def test_adjoint_step_matches_oracle(geom, shape):
+def test_adjoint_step_matches_oracle(geom, shape, mode):
+    """One reverse step against the oracle's dense-Jacobian adjoint, with the
+    bounce-back applied by address selection, by the wall-node branch, and
+    by the automatic choice."""
     from paper_1309_1983_gb300 import capi
     g = GEOMS[geom]
     tau = 0.7
     L = _lat(shape, tau, g)
+    L.set_wall_mode(mode)
     OL = _olat(shape, tau, g)
     f = _random_f(OL, 40)
     F = W.noise((3,) + OL.shape, 41, 2e-3)
