@@ -273,7 +273,8 @@ def extra_workloads(torch, n, steps=100, warmup=10):
 def size_sweep(torch, sizes=(64, 128, 256), steps=1000):
     """The periodic shear-wave sweep: tau = 0.8, u_x = 0.01 sin(2 pi z/N)
     from equilibrium, FP32, `steps` single-update launches per size timed
-    with CUDA events; the wave amplitude (projection of u_x on the initial
+    with CUDA events, then the same steps as one lbm_step call (CUDA-graph
+    replay); the wave amplitude (projection of u_x on the initial
     sine) is sampled every steps/10 updates in an untimed second pass and
     its fitted decay rate compared with nu k^2 (Sec. 5 physics check at every
     size). 64^3 (20 MB per copy) stays resident in the 129 MB L2."""
@@ -288,6 +289,14 @@ def size_sweep(torch, sizes=(64, 128, 256), steps=1000):
         L.init_equilibrium(u=u0)
         L.step(10)
         ms, per = timed_steps(L, steps, torch)
+        # the same steps as one call: replayed CUDA graphs of 32 launches
+        L.step(64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(L.stream)
+        L.step(steps)
+        e1.record(L.stream)
+        e1.synchronize()
+        ms_call = e0.elapsed_time(e1)
         L.init_equilibrium(u=u0)
         sn = torch.sin(2 * np.pi * torch.arange(n, dtype=torch.float64) / n).cuda()
         t, A = [], []
@@ -302,6 +311,7 @@ def size_sweep(torch, sizes=(64, 128, 256), steps=1000):
         mlups = n ** 3 * steps / (ms / 1e3) / 1e6
         out[f"periodic_{n}"] = {
             "mlups": round(mlups, 1), "gbs": round(mlups * 152 / 1e3, 1),
+            "one_call_graph_mlups": round(n ** 3 * steps / ms_call / 1e3, 1),
             "best_step_mlups": round(n ** 3 / (min(per) / 1e3) / 1e6, 1),
             "decay_rate_rel_err": float(rate / (nu * kk * kk) - 1.0),
             "l2_resident": 152 * n ** 3 < 129e6}

@@ -154,6 +154,16 @@ int lbm_set_kernel(lbm_t *h, int variant);
 #define LBM_WALLS_SELECT 2
 int lbm_set_wall_mode(lbm_t *h, int mode);
 
+/* Multi-step calls (lbm_step, lbm_step_moments, lbm_run_host with n > 1)
+ * replay CUDA graphs of `steps` consecutive launches instead of launching
+ * each step: one graph per starting buffer, captured on first use on a
+ * private stream and again after any change of the launch configuration
+ * (bind, tau, lid, block, kernel, wall mode). Removes the per-launch gap that
+ * dominates small (L2-resident) lattices. `steps` even in [2, 1024], or 0 for
+ * plain launches only (default 32). While the bound stream is itself being
+ * captured, plain launches are used. Results are identical either way. */
+int lbm_set_graph_steps(lbm_t *h, int steps);
+
 /* Block shape of the pair kernel: bxp pairs along x (a multiple of 32) by
  * `by` rows, bxp * by <= 256. Default: 64 x 4 (or fewer rows for small ny). */
 int lbm_set_pair_block(lbm_t *h, int bxp, int by);

@@ -81,6 +81,7 @@ _SIGNATURES = {
     "lbm_set_kernel": [_vp, _i],
     "lbm_set_pair_block": [_vp, _i, _i],
     "lbm_set_wall_mode": [_vp, _i],
+    "lbm_set_graph_steps": [_vp, _i],
     "lbm_autotune": [_vp, ctypes.c_char_p, _i, _vp, _vp, _vp],
     "lbm_current": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "lbm_init_equilibrium": [_vp, _vp, _vp],

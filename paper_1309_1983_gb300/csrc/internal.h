@@ -154,9 +154,17 @@ struct lbm_lattice {
   int device;
   lbm::Scratch scr;
   // lbm_run_host pipeline (created on first use, released by lbm_destroy)
-  static constexpr int kMaxSlabs = 8;
+  static constexpr int kMaxSlabs = 16;
   cudaStream_t copy_in, copy_out;
   cudaEvent_t ev_start, ev_in[kMaxSlabs], ev_out[kMaxSlabs], ev_done;
   float *stage;  // 3 cells (u0) + 4 cells (rho, u) FP32
   bool pipe_ready;
+  // multi-step calls replay CUDA graphs of graph_steps launches (one graph
+  // per starting buffer); any change of the launch configuration bumps
+  // config_version and the graphs are captured again on next use
+  int graph_steps;  // 0: plain launches only
+  unsigned config_version;
+  cudaStream_t gcap;
+  cudaGraphExec_t gexec[2];
+  unsigned gexec_version[2];
 };

@@ -108,13 +108,54 @@ int ensure_scratch(lbm_t *h) {
   return LBM_OK;
 }
 
-cudaError_t launch_one_step(const lbm_t *h, bool mom, const StepArgs &a) {
+cudaError_t launch_one_step(const lbm_t *h, bool mom, const StepArgs &a, cudaStream_t s) {
   if (h->kernel == LBM_KERNEL_PAIR && h->storage != lbm::kF32)
-    return lbm::launch_step_pair16(h->storage, mom, a, h->pbx, h->pby, h->stream);
+    return lbm::launch_step_pair16(h->storage, mom, a, h->pbx, h->pby, s);
   if ((h->kernel == LBM_KERNEL_BULK || h->kernel == LBM_KERNEL_BULK1) && !mom)
     return lbm::launch_step_bulk(h->storage, a, h->scr.err,
-                                 h->kernel == LBM_KERNEL_BULK1 ? 1 : 0, h->sms, h->stream);
-  return lbm::launch_step(h->storage, mom, a, h->bx, h->by, h->stream);
+                                 h->kernel == LBM_KERNEL_BULK1 ? 1 : 0, h->sms, s);
+  return lbm::launch_step(h->storage, mom, a, h->bx, h->by, s);
+}
+cudaError_t launch_one_step(const lbm_t *h, bool mom, const StepArgs &a) {
+  return launch_one_step(h, mom, a, h->stream);
+}
+
+void drop_graphs(lbm_t *h) {
+  for (int p = 0; p < 2; ++p) {
+    if (h->gexec[p]) cudaGraphExecDestroy(h->gexec[p]);
+    h->gexec[p] = nullptr;
+  }
+}
+
+// The graph of graph_steps steps starting from buffer p (captured on a
+// private stream on first use or after a configuration change).
+int step_graph(lbm_t *h, int p, cudaGraphExec_t *out) {
+  if (h->gexec[p] && h->gexec_version[p] == h->config_version) {
+    *out = h->gexec[p];
+    return LBM_OK;
+  }
+  if (h->gexec[p]) cudaGraphExecDestroy(h->gexec[p]);
+  h->gexec[p] = nullptr;
+  if (!h->gcap)
+    LBM_CUDA(cudaStreamCreateWithFlags(&h->gcap, cudaStreamNonBlocking), "stream create");
+  LBM_CUDA(cudaStreamBeginCapture(h->gcap, cudaStreamCaptureModeThreadLocal), "graph capture");
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < h->graph_steps && e == cudaSuccess; ++k) {
+    const int c = p ^ (k & 1);
+    e = launch_one_step(h, false, make_args(h, h->f[c], h->f[1 - c]), h->gcap);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(h->gcap, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec[p], g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->gexec[p] = nullptr;
+    return cuda_fail(e, "step graph capture");
+  }
+  h->gexec_version[p] = h->config_version;
+  *out = h->gexec[p];
+  return LBM_OK;
 }
 
 // Streams, events and staging of lbm_run_host, created on first use.
@@ -157,6 +198,21 @@ void release_pipeline(lbm_t *h) {
 }
 
 int do_steps(lbm_t *h, int n, float *rho, float *u) {
+  // whole graphs first (an even number of steps each, so the current buffer
+  // is unchanged), then plain launches; a step writing rho, u is always plain
+  const int G = h->graph_steps;
+  if (G > 0 && n - (rho ? 1 : 0) >= G) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LBM_CUDA(cudaStreamIsCapturing(h->stream, &cs), "stream query");
+    if (cs == cudaStreamCaptureStatusNone) {
+      cudaGraphExec_t ge = nullptr;
+      int rc = step_graph(h, h->cur, &ge);
+      if (rc) return rc;
+      const int reps = (n - (rho ? 1 : 0)) / G;
+      for (int r = 0; r < reps; ++r) LBM_CUDA(cudaGraphLaunch(ge, h->stream), "graph launch");
+      n -= reps * G;
+    }
+  }
   for (int k = 0; k < n; ++k) {
     StepArgs a = make_args(h, h->f[h->cur], h->f[1 - h->cur]);
     const bool mom = (rho != nullptr) && (k == n - 1);
@@ -263,6 +319,11 @@ int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
   h->device = -1;
   h->stage = nullptr;
   h->pipe_ready = false;
+  h->graph_steps = 32;
+  h->config_version = 0;
+  h->gcap = nullptr;
+  h->gexec[0] = h->gexec[1] = nullptr;
+  h->gexec_version[0] = h->gexec_version[1] = 0;
   *out = h;
   return LBM_OK;
 }
@@ -270,6 +331,8 @@ int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
 int lbm_destroy(lbm_t *h) {
   if (!h) return LBM_OK;
   release_pipeline(h);
+  drop_graphs(h);
+  if (h->gcap) cudaStreamDestroy(h->gcap);
   if (h->scr.partials) cudaFree(h->scr.partials);
   delete h;
   return LBM_OK;
@@ -307,6 +370,7 @@ int lbm_bind(lbm_t *h, void *f_a, void *f_b, const float *force, void *stream) {
   h->force = force;
   h->stream = static_cast<cudaStream_t>(stream);
   h->bound = true;
+  h->config_version++;
   return LBM_OK;
 }
 
@@ -318,6 +382,7 @@ int lbm_set_lid(lbm_t *h, float ux, float uy, float uz) {
   h->lid[0] = ux;
   h->lid[1] = uy;
   h->lid[2] = uz;
+  h->config_version++;
   return LBM_OK;
 }
 
@@ -325,6 +390,7 @@ int lbm_set_tau(lbm_t *h, float tau) {
   if (!h) return fail(LBM_EINVAL, "NULL handle");
   if (!(tau > 0.5f) || !isfinite(tau)) return fail(LBM_EINVAL, "tau must be > 1/2");
   h->tau = tau;
+  h->config_version++;
   return LBM_OK;
 }
 
@@ -334,6 +400,7 @@ int lbm_set_block(lbm_t *h, int bx, int by) {
     return fail(LBM_EINVAL, "block must be bx%32==0, by>=1, bx*by<=256");
   h->bx = bx;
   h->by = by;
+  h->config_version++;
   return LBM_OK;
 }
 
@@ -345,6 +412,7 @@ int lbm_set_kernel(lbm_t *h, int variant) {
   if (variant == LBM_KERNEL_PAIR && h->storage == lbm::kF32)
     return fail(LBM_EINVAL, "the pair kernel needs 16-bit storage");
   h->kernel = variant;
+  h->config_version++;
   return LBM_OK;
 }
 
@@ -352,6 +420,16 @@ int lbm_set_wall_mode(lbm_t *h, int mode) {
   if (!h) return fail(LBM_EINVAL, "NULL handle");
   if (mode < LBM_WALLS_AUTO || mode > LBM_WALLS_SELECT) return fail(LBM_EINVAL, "bad mode");
   h->wall_mode = mode;
+  h->config_version++;
+  return LBM_OK;
+}
+
+int lbm_set_graph_steps(lbm_t *h, int steps) {
+  if (!h) return fail(LBM_EINVAL, "NULL handle");
+  if (steps < 0 || steps > 1024 || (steps & 1))
+    return fail(LBM_EINVAL, "graph steps must be even, in [0, 1024]");
+  h->graph_steps = steps;
+  drop_graphs(h);
   return LBM_OK;
 }
 
@@ -361,6 +439,7 @@ int lbm_set_pair_block(lbm_t *h, int bxp, int by) {
     return fail(LBM_EINVAL, "pair block must be bxp%32==0, by>=1, bxp*by<=256");
   h->pbx = bxp;
   h->pby = by;
+  h->config_version++;
   return LBM_OK;
 }
 

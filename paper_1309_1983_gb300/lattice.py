@@ -120,6 +120,11 @@ class Lattice:
              "bulk": capi.LBM_KERNEL_BULK, "bulk1": capi.LBM_KERNEL_BULK1}[variant]
         capi.call("lbm_set_kernel", self._h, v)
 
+    def set_graph_steps(self, steps):
+        """Steps per replayed CUDA graph in multi-step calls (0 = plain
+        launches; see lbm_set_graph_steps)."""
+        capi.call("lbm_set_graph_steps", self._h, int(steps))
+
     def set_wall_mode(self, mode):
         """"auto", "branch" or "select" (see lbm_set_wall_mode)."""
         v = {"auto": capi.LBM_WALLS_AUTO, "branch": capi.LBM_WALLS_BRANCH,

@@ -6,11 +6,21 @@ That data is not available here, so the check is the convergence itself:
 the same cavity at successive resolutions N (Eq. 8 with L = N gives
 tau = 1/2 + 3 N U / Re), each run to a steady state, and the profile
 u_x(z)/U on the vertical centre line compared on the coarsest lattice's
-node positions. Halfway bounce-back makes the scheme second order, so the
-change between successive resolutions should shrink by about 4 per doubling.
+node positions. Observed on GB300 (FP32): the differences shrink by 1.6 to
+2.7 per doubling (order 0.7 to 1.4, in max and RMS norm and in the vortex
+strength u_min alike) rather than 4: the classical cavity's lid meets the
+side walls with a jump in velocity, a singularity that degrades the
+convergence of the whole flow whichever way the lattice is refined.
+
+Two ways to refine: acoustic scaling keeps the lid speed U (the Mach number)
+fixed, so tau - 1/2 grows with N and BGK's viscosity-dependent bounce-back
+wall error does not vanish; diffusive scaling keeps tau fixed and lowers
+U = Re (tau - 1/2) / (3 N), so for a smooth flow lattice and compressibility
+errors both fall as N^-2.
 
 Command line (writes one JSON object):
 
+    python -m paper_1309_1983_gb300.validation --re 400 --sizes 48,96,192 --tau 0.53
     python -m paper_1309_1983_gb300.validation --re 400 --sizes 48,96,192 --u 0.1
 """
 
@@ -29,6 +39,11 @@ from . import perfmodel as PM
 def tau_for(N: int, U: float, Re: float) -> float:
     """Relaxation time giving Reynolds number Re on an N^3 cavity (Eq. 8)."""
     return 0.5 + 3.0 * N * U / Re
+
+
+def lid_for(N: int, tau: float, Re: float) -> float:
+    """Lid speed giving Reynolds number Re on an N^3 cavity at fixed tau (Eq. 8)."""
+    return Re * (tau - 0.5) / (3.0 * N)
 
 
 def centre_profile(N: int, Re: float, U: float = 0.05, tol: float = 2e-5,
@@ -67,20 +82,33 @@ def centre_profile(N: int, Re: float, U: float = 0.05, tol: float = 2e-5,
     return z, prof, steps, converged
 
 
-def self_convergence(Re: float, sizes=(24, 48, 96), U: float = 0.05, **kw):
+def self_convergence(Re: float, sizes=(24, 48, 96), U: float = 0.05, tau: float = None, **kw):
     """Profiles at each size, interpolated to the coarsest lattice's nodes,
     and the successive maximum differences d_k = max |p_{k+1} - p_k| with
-    their ratios (about 4 at second order when the sizes double)."""
-    runs = [centre_profile(N, Re, U, **kw) for N in sizes]
+    their ratios. With ``tau`` given, diffusive scaling (fixed tau, lid speed
+    from Eq. 8 per size); else acoustic scaling at lid speed U."""
+    Us = [lid_for(N, tau, Re) if tau is not None else U for N in sizes]
+    runs = [centre_profile(N, Re, u, **kw) for N, u in zip(sizes, Us)]
     zc = runs[0][0]
     on_coarse = [np.interp(zc, z, p) for z, p, _, _ in runs]
     diffs = [float(np.abs(on_coarse[k + 1] - on_coarse[k]).max())
              for k in range(len(sizes) - 1)]
     ratios = [diffs[k] / diffs[k + 1] for k in range(len(diffs) - 1)]
-    return {"Re": Re, "U": U, "sizes": list(sizes),
-            "tau": [tau_for(N, U, Re) for N in sizes],
+    rms = [float(np.sqrt(np.mean((on_coarse[k + 1] - on_coarse[k]) ** 2)))
+           for k in range(len(sizes) - 1)]
+    # strength of the primary vortex on the centre line, from each run's own
+    # nodes (a parabola through the minimum and its neighbours)
+    umin = []
+    for z, p, _, _ in runs:
+        k = int(np.clip(np.argmin(p), 1, len(p) - 2))
+        a, b, c = np.polyfit(z[k - 1:k + 2], p[k - 1:k + 2], 2)
+        umin.append(float(c - b * b / (4 * a)) if a > 0 else float(p[k]))
+    return {"Re": Re, "scaling": "diffusive" if tau is not None else "acoustic",
+            "U": Us, "sizes": list(sizes),
+            "tau": [tau_for(N, u, Re) for N, u in zip(sizes, Us)],
             "steps": [r[2] for r in runs], "converged": [r[3] for r in runs],
-            "diffs": diffs, "ratios": ratios,
+            "diffs": diffs, "ratios": ratios, "rms_diffs": rms, "u_min": umin,
+            "observed_order": [float(np.log2(r)) for r in ratios],
             "z": zc.tolist(), "profiles_on_coarse": [p.tolist() for p in on_coarse]}
 
 
@@ -88,11 +116,13 @@ def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     p.add_argument("--re", type=float, required=True)
     p.add_argument("--sizes", default="24,48,96")
-    p.add_argument("--u", type=float, default=0.05)
+    p.add_argument("--u", type=float, default=0.05, help="lid speed (acoustic scaling)")
+    p.add_argument("--tau", type=float, default=None, help="fixed tau (diffusive scaling)")
     p.add_argument("--tol", type=float, default=2e-5)
     a = p.parse_args(argv)
     t0 = time.time()
-    out = self_convergence(a.re, tuple(int(s) for s in a.sizes.split(",")), a.u, tol=a.tol)
+    out = self_convergence(a.re, tuple(int(s) for s in a.sizes.split(",")), a.u, tau=a.tau,
+                           tol=a.tol)
     out["seconds"] = round(time.time() - t0, 1)
     print(json.dumps(out))
     return 0

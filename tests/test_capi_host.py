@@ -84,6 +84,18 @@ def test_unbound_handle_is_reported(lib):
         lib.lbm_destroy(h)
 
 
+def test_graph_steps_validation(lib):
+    h = capi.create(8, 8, 8, 0.8, 0)
+    try:
+        for bad in (-2, 3, 1026):
+            assert lib.lbm_set_graph_steps(h, bad) == capi.LBM_EINVAL
+        for ok in (0, 2, 64, 1024):
+            assert lib.lbm_set_graph_steps(h, ok) == 0
+    finally:
+        lib.lbm_destroy(h)
+    assert lib.lbm_set_graph_steps(None, 2) == capi.LBM_EINVAL
+
+
 def test_autotune_rejects_bad_arguments(lib):
     assert lib.lbm_autotune(None, None, 5, None, None, None) == capi.LBM_EINVAL
     assert lib.lbm_batch_autotune(None, None, 5, None, None, None) == capi.LBM_EINVAL
