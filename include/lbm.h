@@ -73,6 +73,7 @@ extern "C" {
 #define LBM_STORE_F16 0x10u  /* ... as FP16, round to nearest even (76 B) */
 #define LBM_STORE_BF16 0x20u /* ... as BF16, round to nearest even (76 B) */
 #define LBM_FORCE 0x40u      /* read a per-cell body force F each step */
+#define LBM_ADJOINT 0x80u    /* the handle will run the adjoint (FP32 storage only) */
 #define LBM_CAVITY (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z | LBM_LID)
 
 typedef struct lbm_lattice lbm_t;
@@ -97,7 +98,8 @@ const char *lbm_last_error(void);
 /* Create a lattice of nx * ny * nz nodes with relaxation time tau (Eq. 3)
  * and LBM_* flags. Host-only: no CUDA call is made. Requires every size >= 1,
  * tau > 1/2, at most one LBM_STORE_* value, LBM_LID only with LBM_WALL_Z,
- * and nz * ny * pitch < 2^31. On success *out owns the handle. */
+ * LBM_ADJOINT only with FP32 storage, and nz * ny * pitch < 2^31. On
+ * success *out owns the handle. */
 int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
                lbm_t **out);
 
@@ -106,6 +108,18 @@ int lbm_destroy(lbm_t *h);
 
 /* Buffer layout of the handle (sizes the caller must allocate). */
 int lbm_get_layout(const lbm_t *h, lbm_layout_t *out);
+
+/* Bytes of one caller-owned buffer of the given kind: one f buffer, the
+ * force field, rho, u, one adjoint (lambda) buffer, or the force gradient.
+ * The same figures as lbm_get_layout, one at a time. LBM_EINVAL for a NULL
+ * argument or an unknown kind. */
+#define LBM_BUF_F 0
+#define LBM_BUF_FORCE 1
+#define LBM_BUF_RHO 2
+#define LBM_BUF_U 3
+#define LBM_BUF_LAMBDA 4
+#define LBM_BUF_GRADF 5
+int lbm_buffer_bytes(const lbm_t *h, int which, size_t *bytes);
 
 /* Bind two caller-owned device f buffers of layout.f_bytes each (256-byte
  * aligned), an optional force field [3][nz][ny][nx] (required iff LBM_FORCE),

@@ -33,6 +33,8 @@ LBM_STORE_F32 = 0x00
 LBM_STORE_F16 = 0x10
 LBM_STORE_BF16 = 0x20
 LBM_FORCE = 0x40
+LBM_ADJOINT = 0x80
+LBM_BUF_F, LBM_BUF_FORCE, LBM_BUF_RHO, LBM_BUF_U, LBM_BUF_LAMBDA, LBM_BUF_GRADF = range(6)
 LBM_CAVITY = LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z | LBM_LID
 LBM_WALLS_AUTO = 0
 LBM_WALLS_BRANCH = 1
@@ -74,6 +76,7 @@ _SIGNATURES = {
     "lbm_create": [_i, _i, _i, _f, _u32, ctypes.POINTER(_vp)],
     "lbm_destroy": [_vp],
     "lbm_get_layout": [_vp, ctypes.POINTER(Layout)],
+    "lbm_buffer_bytes": [_vp, _i, ctypes.POINTER(ctypes.c_size_t)],
     "lbm_bind": [_vp, _vp, _vp, _vp, _vp],
     "lbm_set_lid": [_vp, _f, _f, _f],
     "lbm_set_tau": [_vp, _f],

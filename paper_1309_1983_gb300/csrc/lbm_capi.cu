@@ -39,7 +39,7 @@ int cuda_fail(cudaError_t e, const char *where) {
 
 constexpr uint32_t kKnownFlags = LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z |
                                  LBM_LID | LBM_STORE_F16 | LBM_STORE_BF16 |
-                                 LBM_FORCE;
+                                 LBM_FORCE | LBM_ADJOINT;
 
 StepArgs make_args(const lbm_t *h, const void *fin, void *fout) {
   StepArgs a;
@@ -283,6 +283,7 @@ int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
     return fail(LBM_EINVAL, "more than one storage type");
   if ((flags & LBM_LID) && !(flags & LBM_WALL_Z))
     return fail(LBM_EINVAL, "LBM_LID needs LBM_WALL_Z");
+  if ((flags & LBM_ADJOINT) && st) return fail(LBM_EINVAL, "LBM_ADJOINT needs FP32 storage");
   const int storage = st == LBM_STORE_F16 ? lbm::kF16
                       : st == LBM_STORE_BF16 ? lbm::kBF16 : lbm::kF32;
   const int eb = storage == lbm::kF32 ? 4 : 2;
@@ -351,6 +352,22 @@ int lbm_get_layout(const lbm_t *h, lbm_layout_t *out) {
   const size_t pitch32 = ((size_t)h->nx + 7) / 8 * 8;
   out->lambda_bytes = (size_t)lbm::Q * pitch32 * h->ny * h->nz * 4;
   out->cells = (size_t)h->nx * h->ny * h->nz;
+  return LBM_OK;
+}
+
+int lbm_buffer_bytes(const lbm_t *h, int which, size_t *bytes) {
+  if (!h || !bytes) return fail(LBM_EINVAL, "NULL argument");
+  lbm_layout_t L;
+  lbm_get_layout(h, &L);
+  switch (which) {
+    case LBM_BUF_F: *bytes = L.f_bytes; break;
+    case LBM_BUF_RHO: *bytes = L.cells * sizeof(float); break;
+    case LBM_BUF_FORCE:
+    case LBM_BUF_U:
+    case LBM_BUF_GRADF: *bytes = 3 * L.cells * sizeof(float); break;
+    case LBM_BUF_LAMBDA: *bytes = L.lambda_bytes; break;
+    default: return fail(LBM_EINVAL, "unknown buffer kind");
+  }
   return LBM_OK;
 }
 

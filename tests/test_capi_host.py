@@ -84,6 +84,33 @@ def test_unbound_handle_is_reported(lib):
         lib.lbm_destroy(h)
 
 
+def test_buffer_bytes_match_layout(lib):
+    h = capi.create(37, 11, 9, 0.8, capi.LBM_STORE_F16)
+    try:
+        L = capi.layout(h)
+        want = {capi.LBM_BUF_F: L.f_bytes, capi.LBM_BUF_FORCE: 12 * L.cells,
+                capi.LBM_BUF_RHO: 4 * L.cells, capi.LBM_BUF_U: 12 * L.cells,
+                capi.LBM_BUF_LAMBDA: L.lambda_bytes, capi.LBM_BUF_GRADF: 12 * L.cells}
+        for which, nbytes in want.items():
+            b = ctypes.c_size_t()
+            assert lib.lbm_buffer_bytes(h, which, ctypes.byref(b)) == 0
+            assert b.value == nbytes, which
+        b = ctypes.c_size_t()
+        assert lib.lbm_buffer_bytes(h, 6, ctypes.byref(b)) == capi.LBM_EINVAL
+        assert lib.lbm_buffer_bytes(h, 0, None) == capi.LBM_EINVAL
+    finally:
+        lib.lbm_destroy(h)
+
+
+def test_adjoint_flag_needs_fp32(lib):
+    h = ctypes.c_void_p()
+    assert lib.lbm_create(8, 8, 8, ctypes.c_float(0.8), capi.LBM_ADJOINT | capi.LBM_STORE_BF16,
+                          ctypes.byref(h)) == capi.LBM_EINVAL
+    assert lib.lbm_create(8, 8, 8, ctypes.c_float(0.8), capi.LBM_ADJOINT | capi.LBM_CAVITY,
+                          ctypes.byref(h)) == 0
+    lib.lbm_destroy(h)
+
+
 def test_graph_steps_validation(lib):
     h = capi.create(8, 8, 8, 0.8, 0)
     try:
