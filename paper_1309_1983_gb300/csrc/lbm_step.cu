@@ -27,17 +27,20 @@ namespace lbm {
 #define LBM_STEP_BOUNDS __launch_bounds__(256)
 #endif
 
-template <int S, bool WALLS, bool FORCE, bool MOM>
+// W: 0 periodic, 1 walls by address selection, 2 walls by the wall-node
+// branch (separate kernels: compiling both wall forms into one kernel cost
+// ~50 instructions per node even though only one runs).
+template <int S, int W, bool FORCE, bool MOM>
 __global__ void LBM_STEP_BOUNDS k_step(const StepArgs a) {
   using T = typename Store<S>::T;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = a.z0 + blockIdx.z;
   if (x >= a.nx || y >= a.ny) return;
-  step_node<S, WALLS, FORCE, MOM, false>(
+  step_node<S, (W != 0), FORCE, MOM, false>(
       static_cast<const T *>(a.fin), static_cast<T *>(a.fout), a.nx, a.ny, a.nz, a.pitch,
       a.plane, a.walls, a.lidc, a.omega, a.kf, a.force, a.rho, a.u, a.cells, x, y, z,
-      a.wall_select != 0);
+      W == 1);
 }
 
 template <int S>
@@ -149,20 +152,25 @@ static dim3 node_grid(const StepArgs &a, int bx, int by) {
 template <int S>
 static void step_dispatch(bool moments, const StepArgs &a, dim3 g, dim3 b,
                           cudaStream_t s) {
-  const bool walls = a.walls != 0, force = a.force != nullptr;
+  const int walls = a.walls == 0 ? 0 : a.wall_select ? 1 : 2;
+  const bool force = a.force != nullptr;
 #define LBM_STEP_CASE(W, F, M)                                  \
   if (walls == W && force == F && moments == M) {               \
     k_step<S, W, F, M><<<g, b, 0, s>>>(a);                      \
     return;                                                     \
   }
-  LBM_STEP_CASE(false, false, false)
-  LBM_STEP_CASE(false, false, true)
-  LBM_STEP_CASE(false, true, false)
-  LBM_STEP_CASE(false, true, true)
-  LBM_STEP_CASE(true, false, false)
-  LBM_STEP_CASE(true, false, true)
-  LBM_STEP_CASE(true, true, false)
-  LBM_STEP_CASE(true, true, true)
+  LBM_STEP_CASE(0, false, false)
+  LBM_STEP_CASE(0, false, true)
+  LBM_STEP_CASE(0, true, false)
+  LBM_STEP_CASE(0, true, true)
+  LBM_STEP_CASE(1, false, false)
+  LBM_STEP_CASE(1, false, true)
+  LBM_STEP_CASE(1, true, false)
+  LBM_STEP_CASE(1, true, true)
+  LBM_STEP_CASE(2, false, false)
+  LBM_STEP_CASE(2, false, true)
+  LBM_STEP_CASE(2, true, false)
+  LBM_STEP_CASE(2, true, true)
 #undef LBM_STEP_CASE
 }
 

@@ -104,22 +104,45 @@ __device__ __forceinline__ void gather_walled(const typename Store<S>::T *__rest
   });
 }
 
+// Value of a bounced pull: f_ibar(x), plus the moving-wall term when the
+// outside source x - e_i lies on the plane z = nz (e_z = -1 at the top face).
+template <int S, bool L2ONLY, int i>
+__device__ __forceinline__ float bounced_value(const typename Store<S>::T *__restrict__ fin,
+                                               uint32_t plane, const NodeIdx &n,
+                                               const float (&lidc)[Q]) {
+  float v = load_f<S, L2ONLY>(fin + (size_t)kOpp_v<i> * plane + n.c);
+  if constexpr (kEz[i] == -1) v += n.z1 ? lidc[i] : 0.0f;
+  return v;
+}
+
+// Re-read, on a node of one walled face, the directions whose pull source
+// lies beyond that face: component `axis` of e_i equal to `sgn`.
+template <int S, bool L2ONLY, int axis, int sgn>
+__device__ __forceinline__ void fix_face(const typename Store<S>::T *__restrict__ fin,
+                                         uint32_t plane, const NodeIdx &n,
+                                         const float (&lidc)[Q], float (&d)[Q]) {
+  static_for<1, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int e = axis == 0 ? kEx[i] : axis == 1 ? kEy[i] : kEz[i];
+    if constexpr (e == sgn) d[i] = bounced_value<S, L2ONLY, i>(fin, plane, n, lidc);
+  });
+}
+
 // Halfway bounce-back applied after a plain periodic gather, only on nodes
 // that touch a walled face (a branch; cheaper than gather_walled when wall
-// nodes are a small fraction of each warp's nodes, i.e. on long rows).
+// nodes are a small fraction of each warp's nodes, i.e. on long rows). Each
+// face re-reads only its five inward directions; a direction bouncing on two
+// faces (edges, corners) is written twice with the same value.
 template <int S, bool L2ONLY = false>
 __device__ __forceinline__ void bounce_fixup(const typename Store<S>::T *__restrict__ fin,
                                              uint32_t plane, const NodeIdx &n,
                                              const float (&lidc)[Q], float (&d)[Q]) {
-  if (!on_wall(n)) return;
-  static_for<1, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    if (bounces<i>(n)) {
-      float v = load_f<S, L2ONLY>(fin + (size_t)kOpp_v<i> * plane + n.c);
-      if constexpr (kEz[i] == -1) v += n.z1 ? lidc[i] : 0.0f;
-      d[i] = v;
-    }
-  });
+  if (n.x0) fix_face<S, L2ONLY, 0, 1>(fin, plane, n, lidc, d);
+  if (n.x1) fix_face<S, L2ONLY, 0, -1>(fin, plane, n, lidc, d);
+  if (n.y0) fix_face<S, L2ONLY, 1, 1>(fin, plane, n, lidc, d);
+  if (n.y1) fix_face<S, L2ONLY, 1, -1>(fin, plane, n, lidc, d);
+  if (n.z0) fix_face<S, L2ONLY, 2, 1>(fin, plane, n, lidc, d);
+  if (n.z1) fix_face<S, L2ONLY, 2, -1>(fin, plane, n, lidc, d);
 }
 
 // One fused update of node (x, y, z) (Alg. 3): pull gather, boundary rule,

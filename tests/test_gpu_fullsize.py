@@ -116,3 +116,55 @@ def test_mass_conserved_at_full_size():
         L.close()
         del L
         torch.cuda.empty_cache()
+
+
+def _ulp16(x, storage):
+    """Spacing of the 16-bit storage format at |x| (FP16: 10 mantissa bits,
+    subnormal below 2^-14; BF16: 7 mantissa bits)."""
+    a = np.maximum(np.abs(x), 1e-30)
+    e = np.floor(np.log2(a))
+    if storage == "f16":
+        return 2.0 ** (np.maximum(e, -14) - 10)
+    return 2.0 ** (e - 7)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_16bit_cavity_384_sampled_parity(storage):
+    """FP16 / BF16 storage at 384^3 in the benchmark's cavity configuration
+    (default launch, tau = 0.55, lid 0.05): one step from a developed state,
+    sampled nodes against the FP64 oracle applied to the stored 16-bit inputs.
+    The stored result may differ from the exactly computed one by the final
+    rounding to 16 bits plus FP32 arithmetic: at most one unit in the last
+    place of the format at that value, with a 1e-8 floor for values near 0."""
+    from paper_1309_1983_gb300.lattice import Lattice
+    tau, lid = 0.55, (0.05, 0.0, 0.0)
+    L = Lattice(N, N, N, tau, walls=(True, True, True), lid=lid, storage=storage)
+    L.init_equilibrium()
+    L.step(20)
+    w = O.weights()
+    dt = torch.float16 if storage == "f16" else torch.bfloat16
+
+    def view():
+        cur, _ = L.current_buffers()
+        return cur.view(dt).view(19, L.nz, L.ny, L.layout.pitch)
+
+    samples = _samples(N, np.random.default_rng(3), count=30)
+    v = view()
+    blocks = []
+    for (x, y, z) in samples:
+        xi, cx, wx = _axis_block(N, x, True)
+        yi, cy, wy = _axis_block(N, y, True)
+        zi, cz, wz = _axis_block(N, z, True)
+        sub = v[:, zi][:, :, yi][:, :, :, xi].double().cpu().numpy() + w[:, None, None, None]
+        OL = O.Lattice(len(xi), len(yi), len(zi), tau, walls=(wx, wy, wz), lid=wz,
+                       lid_u=lid)
+        blocks.append((sub, OL, (cx, cy, cz)))
+    L.step(1)
+    v = view()
+    for (x, y, z), (sub, OL, (cx, cy, cz)) in zip(samples, blocks):
+        ref = O.run(OL, sub, 1)[:, cz, cy, cx] - w
+        got = v[:, z, y, x].double().cpu().numpy()
+        err = np.abs(got - ref)
+        # + 1e-8: the FP32 arithmetic on values near zero (a corner at rest
+        # stores exactly 0 where the FP64 reference leaves ~1e-16)
+        assert (err <= 1.0001 * _ulp16(ref, storage) + 1e-8).all(), ((x, y, z), err.max())
