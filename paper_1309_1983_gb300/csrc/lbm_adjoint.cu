@@ -22,17 +22,19 @@ struct AdjArgs {
 #define LBM_ADJ_MIN_BLOCKS 3
 #endif
 
-template <bool WALLS, bool FORCE, bool GRADF>
+// W: 0 periodic, 1 walls by address selection, 2 walls by the wall-node
+// branch (one kernel per form: a runtime choice compiles both into one).
+template <int W, bool FORCE, bool GRADF>
 __global__ void __launch_bounds__(256, LBM_ADJ_MIN_BLOCKS) k_adjoint_step(const AdjArgs a) {
   const StepArgs &g = a.g;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= g.nx || y >= g.ny) return;
-  adjoint_node<WALLS, FORCE, GRADF>(static_cast<const float *>(g.fin), a.lam_in, a.lam_out,
-                                    g.force, a.grad_force, g.nx, g.ny, g.nz, g.pitch, g.plane,
-                                    g.walls, g.lidc, g.omega, g.kf, g.cells, x, y, z,
-                                    g.wall_select != 0);
+  adjoint_node<(W != 0), FORCE, GRADF>(static_cast<const float *>(g.fin), a.lam_in, a.lam_out,
+                                       g.force, a.grad_force, g.nx, g.ny, g.nz, g.pitch,
+                                       g.plane, g.walls, g.lidc, g.omega, g.kf, g.cells, x, y,
+                                       z, W == 1);
 }
 
 // Seed over all nodes (grid stride), FP64 loss partials per block.
@@ -76,18 +78,27 @@ cudaError_t launch_adjoint_step(const StepArgs &g, const float *lam_in,
   a.u_target = nullptr;
   a.partials = nullptr;
   const dim3 grid((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz), blk(bx, by, 1);
-  const int v = (g.walls ? 4 : 0) | (g.force ? 2 : 0) | (grad_force ? 1 : 0);
-  switch (v) {
-    case 0: k_adjoint_step<false, false, false><<<grid, blk, 0, s>>>(a); break;
-    case 1: k_adjoint_step<false, false, true><<<grid, blk, 0, s>>>(a); break;
-    case 2: k_adjoint_step<false, true, false><<<grid, blk, 0, s>>>(a); break;
-    case 3: k_adjoint_step<false, true, true><<<grid, blk, 0, s>>>(a); break;
-    case 4: k_adjoint_step<true, false, false><<<grid, blk, 0, s>>>(a); break;
-    case 5: k_adjoint_step<true, false, true><<<grid, blk, 0, s>>>(a); break;
-    case 6: k_adjoint_step<true, true, false><<<grid, blk, 0, s>>>(a); break;
-    default: k_adjoint_step<true, true, true><<<grid, blk, 0, s>>>(a); break;
+  const int w = g.walls == 0 ? 0 : g.wall_select ? 1 : 2;
+  const bool F = g.force != nullptr, G = grad_force != nullptr;
+#define LBM_ADJ_CASE(W_, F_, G_)                                 \
+  if (w == W_ && F == F_ && G == G_) {                           \
+    k_adjoint_step<W_, F_, G_><<<grid, blk, 0, s>>>(a);          \
+    return cudaGetLastError();                                   \
   }
-  return cudaGetLastError();
+  LBM_ADJ_CASE(0, false, false)
+  LBM_ADJ_CASE(0, false, true)
+  LBM_ADJ_CASE(0, true, false)
+  LBM_ADJ_CASE(0, true, true)
+  LBM_ADJ_CASE(1, false, false)
+  LBM_ADJ_CASE(1, false, true)
+  LBM_ADJ_CASE(1, true, false)
+  LBM_ADJ_CASE(1, true, true)
+  LBM_ADJ_CASE(2, false, false)
+  LBM_ADJ_CASE(2, false, true)
+  LBM_ADJ_CASE(2, true, false)
+  LBM_ADJ_CASE(2, true, true)
+#undef LBM_ADJ_CASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_adjoint_seed(const StepArgs &g, const float *u_target,

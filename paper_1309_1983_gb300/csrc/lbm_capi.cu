@@ -756,10 +756,11 @@ int lbm_adjoint_step(lbm_t *h, const void *f_n, const float *lambda_in,
     return fail(LBM_EINVAL, "bad buffers");
   StepArgs g = make_args(h, f_n, nullptr);
   // The adjoint issues ~1.7x the forward's instructions per node: the branch
-  // form (fewer instructions off the walls) wins once rows are long, and
+  // form (fewer instructions off the walls) wins from 64-node rows on
+  // (measured at 128^3 and 256^3), and
   // 64 x 2 blocks measured best for both periodic and walled lattices.
   g.wall_select = h->wall_mode == LBM_WALLS_SELECT ||
-                  (h->wall_mode == LBM_WALLS_AUTO && h->nx < 256);
+                  (h->wall_mode == LBM_WALLS_AUTO && h->nx < 64);
   const int abx = h->nx <= 32 ? 32 : 64;
   cudaError_t e = lbm::launch_adjoint_step(g, lambda_in, lambda_out, grad_force, abx,
                                            128 / abx, h->stream);
