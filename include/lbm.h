@@ -220,6 +220,11 @@ int lbm_step_moments(lbm_t *h, int n, float *rho, float *u);
  * current-state pointer are not touched. */
 int lbm_step_to(lbm_t *h, const void *f_in, void *f_out);
 
+/* As lbm_step_to, also writing the density rho [nz][ny][nx] and velocity
+ * u [3][nz][ny][nx] (device FP32) that the step's collision used: the inputs
+ * of lbm_adjoint_step_moments for this step. */
+int lbm_step_to_moments(lbm_t *h, const void *f_in, void *f_out, float *rho, float *u);
+
 /* Push iteration (Alg. 2) for the streaming-order comparison of Sec. 4.2:
  * g_in and g_out hold POST-STREAMING distributions (layout and storage as
  * the f buffers); each node reads its own values (aligned), collides, and
@@ -325,6 +330,16 @@ int lbm_adjoint_seed(lbm_t *h, const void *f_T, const float *u_target,
 int lbm_adjoint_step(lbm_t *h, const void *f_n, const float *lambda_in,
                      float *lambda_out, float *grad_force);
 
+/* The same reverse step from the moments instead of the state: rho_n
+ * [nz][ny][nx] and u_n [3][nz][ny][nx] (device FP32) as lbm_step_moments or
+ * lbm_step_to_moments wrote them for the forward step from f^n. The
+ * collision Jacobian depends on the pulled state only through rho and u, so
+ * the result is bit-identical to lbm_adjoint_step(f_n, ...) and the step
+ * reads 16 bytes per node instead of gathering 76. Same launch and wall
+ * rules and the same errors as lbm_adjoint_step. */
+int lbm_adjoint_step_moments(lbm_t *h, const float *rho_n, const float *u_n,
+                             const float *lambda_in, float *lambda_out, float *grad_force);
+
 /* grad_u0 = sum_i lambda^0_i d f^eq_i(1, u0) / du0 (Eq. 5) for an initial
  * state f^0 = f^eq(1, u0); u0 may be NULL (zero velocity). Device buffers:
  * lambda0 FP32 lambda layout, u0 and grad_u0 [3][nz][ny][nx]. */
@@ -416,6 +431,12 @@ int lbm_batch_init_equilibrium(lbm_batch_t *b, const float *u0);
  * layout, no overlap); the bound pair is not touched. */
 int lbm_batch_step_to(lbm_batch_t *b, const void *f_in, void *f_out);
 
+/* As lbm_batch_step_to, also writing every node's collision rho and u into
+ * dense per-domain fields (the layout of lbm_batch_moments): the inputs of
+ * lbm_batch_adjoint_step_moments for this step. */
+int lbm_batch_step_to_moments(lbm_batch_t *b, const void *f_in, void *f_out, float *rho,
+                              float *u);
+
 /* Discrete adjoint over all domains, as lbm_adjoint_seed / _step / _u0 for a
  * single lattice (force F = 0; the force gradient is taken at F = 0). The
  * loss is the sum over domains of 1/2 sum_x |u - u_target|^2 (FP64, device
@@ -425,6 +446,11 @@ int lbm_batch_adjoint_seed(lbm_batch_t *b, const void *f_T, const float *u_targe
                            float *lambda_T, float *grad_force, double *loss);
 int lbm_batch_adjoint_step(lbm_batch_t *b, const void *f_n, const float *lambda_in,
                            float *lambda_out, float *grad_force);
+/* The reverse step from the moments lbm_batch_step_to_moments wrote for the
+ * forward step from f^n (bit-identical to lbm_batch_adjoint_step). */
+int lbm_batch_adjoint_step_moments(lbm_batch_t *b, const float *rho_n, const float *u_n,
+                                   const float *lambda_in, float *lambda_out,
+                                   float *grad_force);
 int lbm_batch_adjoint_u0(lbm_batch_t *b, const float *lambda0, const float *u0,
                          float *grad_u0);
 

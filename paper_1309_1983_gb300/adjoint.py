@@ -6,9 +6,14 @@ L = 1/2 sum_x |u(x, T) - u_target(x)|^2. Gradients with respect to u0 and F
 come from the library's adjoint kernels (lbm_adjoint_seed, lbm_adjoint_step,
 lbm_adjoint_u0, or their lbm_batch_* counterparts for a batch of lattices).
 The forward keeps the states f^0, f^K, f^2K, ...; the backward recomputes
-each segment of K states from its checkpoint (lbm_step_to) and then runs
-the reverse steps over it, so memory holds ceil(T/K) checkpoints plus K - 1
-segment states.
+each segment from its checkpoint and then runs the reverse steps over it.
+By default (``moments=True``) the recompute stores, per step, only the
+density and velocity its collision used (lbm_step_to_moments, 16 bytes per
+node): the collision Jacobian depends on the pulled state only through
+them, so the reverse step (lbm_adjoint_step_moments) reads those instead of
+re-gathering f^n, and a segment needs 16 instead of 76 bytes per node and
+step. ``moments=False`` keeps the K - 1 segment states and re-gathers them
+(lbm_adjoint_step); both give the same bits.
 
 Every array operation runs in the library's kernels; this module only owns
 the torch buffers and orders the calls.
@@ -31,12 +36,14 @@ def _p(t):
 class _Checkpointed:
     """Checkpoint / recompute driver; subclasses supply the kernels."""
 
-    def __init__(self, T, K):
+    def __init__(self, T, K, moments=True):
         if T < 1 or K < 1:
             raise ValueError("T and K must be >= 1")
         self.T, self.K = int(T), int(K)
+        self.moments = bool(moments)
         self._scratch = None
         self._segment = []
+        self._mom_seg = []
         self._ckpt_pool = []
 
     # -- supplied by subclasses ------------------------------------------------
@@ -53,6 +60,15 @@ class _Checkpointed:
         raise NotImplementedError
 
     def _adj_step(self, fn, lam_in, lam_out, gF):
+        raise NotImplementedError
+
+    def _step_mom(self, fin, fout, rho, u):
+        raise NotImplementedError
+
+    def _adj_step_mom(self, rho, u, lam_in, lam_out, gF):
+        raise NotImplementedError
+
+    def _mom(self):  # (rho, u) buffers for one step
         raise NotImplementedError
 
     def _u0grad(self, lam0, u0, gu0):
@@ -93,12 +109,28 @@ class _Checkpointed:
         gF = self._field()
         loss = torch.zeros((), dtype=torch.float64, device=gF.device)
         self._seed(f_T, ut, lam_a, gF, loss)
-        need = min(self.K, self.T) - 1
-        while len(self._segment) < need:
-            self._segment.append(self._fbuf())
+        if self.moments:
+            need = min(self.K, self.T)
+            while len(self._mom_seg) < need:
+                self._mom_seg.append(self._mom())
+        else:
+            need = min(self.K, self.T) - 1
+            while len(self._segment) < need:
+                self._segment.append(self._fbuf())
         for s in range(len(ckpts) - 1, -1, -1):
             start = s * self.K
             stop = min(start + self.K, self.T)
+            if self.moments:
+                # f_T (a scratch buffer) is no longer needed after the seed
+                cur = ckpts[s]
+                for k in range(stop - start):
+                    dst = self._scratch[k % 2]
+                    self._step_mom(cur, dst, *self._mom_seg[k])
+                    cur = dst
+                for n in range(stop - 1, start - 1, -1):
+                    self._adj_step_mom(*self._mom_seg[n - start], lam_a, lam_b, gF)
+                    lam_a, lam_b = lam_b, lam_a
+                continue
             states = [ckpts[s]]
             for k in range(1, stop - start):
                 self._step_to(states[-1], self._segment[k - 1])
@@ -131,8 +163,8 @@ class AdjointProblem(_Checkpointed):
     velocity-mismatch problem on one lattice (FP32 storage)."""
 
     def __init__(self, nx, ny, nz, tau, T, K=50, walls=(False, False, False), lid=None,
-                 device="cuda"):
-        super().__init__(T, K)
+                 device="cuda", moments=True):
+        super().__init__(T, K, moments)
         self.lat = Lattice(nx, ny, nz, tau, walls=walls, lid=lid, storage="f32", force=True,
                            device=device)
         self.shape = self.lat.shape
@@ -164,6 +196,17 @@ class AdjointProblem(_Checkpointed):
     def _adj_step(self, fn, lam_in, lam_out, gF):
         capi.call("lbm_adjoint_step", self.lat.handle, _p(fn), _p(lam_in), _p(lam_out), _p(gF))
 
+    def _step_mom(self, fin, fout, rho, u):
+        capi.call("lbm_step_to_moments", self.lat.handle, _p(fin), _p(fout), _p(rho), _p(u))
+
+    def _adj_step_mom(self, rho, u, lam_in, lam_out, gF):
+        capi.call("lbm_adjoint_step_moments", self.lat.handle, _p(rho), _p(u), _p(lam_in),
+                  _p(lam_out), _p(gF))
+
+    def _mom(self):
+        return (torch.empty(self.shape, dtype=torch.float32, device=self.device),
+                torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device))
+
     def _u0grad(self, lam0, u0, gu0):
         capi.call("lbm_adjoint_u0", self.lat.handle, _p(lam0), _p(u0), _p(gu0))
 
@@ -180,8 +223,8 @@ class BatchAdjointProblem(_Checkpointed):
     the gradients) use the batch's dense per-domain layout, see
     :meth:`~.batch.Batch.pack_vectors`."""
 
-    def __init__(self, batch, T, K=50):
-        super().__init__(T, K)
+    def __init__(self, batch, T, K=50, moments=True):
+        super().__init__(T, K, moments)
         self.b = batch
         self.device = batch.device
 
@@ -203,6 +246,17 @@ class BatchAdjointProblem(_Checkpointed):
     def _adj_step(self, fn, lam_in, lam_out, gF):
         capi.call("lbm_batch_adjoint_step", self.b.handle, _p(fn), _p(lam_in), _p(lam_out),
                   _p(gF))
+
+    def _step_mom(self, fin, fout, rho, u):
+        capi.call("lbm_batch_step_to_moments", self.b.handle, _p(fin), _p(fout), _p(rho), _p(u))
+
+    def _adj_step_mom(self, rho, u, lam_in, lam_out, gF):
+        capi.call("lbm_batch_adjoint_step_moments", self.b.handle, _p(rho), _p(u), _p(lam_in),
+                  _p(lam_out), _p(gF))
+
+    def _mom(self):
+        return (torch.empty(self.b.cells, dtype=torch.float32, device=self.device),
+                torch.empty(3 * self.b.cells, dtype=torch.float32, device=self.device))
 
     def _u0grad(self, lam0, u0, gu0):
         capi.call("lbm_batch_adjoint_u0", self.b.handle, _p(lam0), _p(u0), _p(gu0))

@@ -91,6 +91,7 @@ _SIGNATURES = {
     "lbm_step": [_vp, _i],
     "lbm_step_moments": [_vp, _i, _vp, _vp],
     "lbm_step_to": [_vp, _vp, _vp],
+    "lbm_step_to_moments": [_vp, _vp, _vp, _vp, _vp],
     "lbm_step_push": [_vp, _vp, _vp],
     "lbm_stream": [_vp, _vp, _vp, _i],
     "lbm_moments": [_vp, _vp, _vp, _dp],
@@ -102,6 +103,7 @@ _SIGNATURES = {
     "lbm_run_host": [_vp, _vp, _i, _vp, _vp],
     "lbm_adjoint_seed": [_vp, _vp, _vp, _vp, _vp, _vp],
     "lbm_adjoint_step": [_vp, _vp, _vp, _vp, _vp],
+    "lbm_adjoint_step_moments": [_vp, _vp, _vp, _vp, _vp, _vp],
     "lbm_adjoint_u0": [_vp, _vp, _vp, _vp],
     "lbm_batch_create": [_i, _vp, _vp, _vp, _u32, ctypes.POINTER(_vp)],
     "lbm_batch_destroy": [_vp],
@@ -122,8 +124,10 @@ _SIGNATURES = {
     "lbm_batch_set_f": [_vp, _i, _vp],
     "lbm_batch_init_equilibrium": [_vp, _vp],
     "lbm_batch_step_to": [_vp, _vp, _vp],
+    "lbm_batch_step_to_moments": [_vp, _vp, _vp, _vp, _vp],
     "lbm_batch_adjoint_seed": [_vp, _vp, _vp, _vp, _vp, _vp],
     "lbm_batch_adjoint_step": [_vp, _vp, _vp, _vp, _vp],
+    "lbm_batch_adjoint_step_moments": [_vp, _vp, _vp, _vp, _vp, _vp],
     "lbm_batch_adjoint_u0": [_vp, _vp, _vp, _vp],
 }
 _RESTYPE = {"lbm_strerror": ctypes.c_char_p, "lbm_last_error": ctypes.c_char_p}

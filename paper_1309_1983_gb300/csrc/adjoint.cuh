@@ -66,51 +66,27 @@ __device__ __forceinline__ void mat_vec(const float (&L2)[6], float vx, float vy
   oz = fmaf(L2[4], vx, fmaf(L2[5], vy, L2[2] * vz));
 }
 
-// One reverse step at node (x, y, z): recompute g = P f^n there, form
-// mu = J_C(g)^T lambda^{n+1}(x), scatter it by P^T into lambda_out, and add
-// the force cotangent into gF (GRADF). WALLS = false compiles the periodic
-// form only; with WALLS the gather and the scatter apply the bounce-back rule
-// either by per-direction address selection on every node (wall_select) or
-// only on nodes that touch a walled face (a branch, cheaper on long rows).
-template <bool WALLS, bool FORCE, bool GRADF>
-__device__ __forceinline__ void adjoint_node(
-    const float *__restrict__ fn, const float *__restrict__ lam_in,
-    float *__restrict__ lam_out, const float *__restrict__ force, float *__restrict__ gF,
-    int nx, int ny, int nz, int pitch, uint32_t plane, uint32_t walls,
-    const float (&lidc)[Q], float omega, float kf, uint32_t cells, int x, int y, int z,
-    bool wall_select = true) {
-  const NodeIdx n = node_index(nx, ny, nz, pitch, WALLS ? walls : 0u, x, y, z);
-  // bounce-back handled per direction on this node (uniform when selecting)
-  const bool sel = WALLS && (wall_select || on_wall(n));
-
-  // recompute the post-streaming state g = P f^n of the forward step
-  // (measured faster here than a periodic gather plus face fix-ups)
-  float d[Q];
-  if (sel)
-    gather_walled<0>(fn, plane, n, lidc, d);
-  else
-    gather<0>(fn, plane, n, d);
-
-  float lam[Q];
+// lambda^{n+1} at the node (aligned loads).
+__device__ __forceinline__ void load_lambda(const float *__restrict__ lam_in, uint32_t plane,
+                                            const NodeIdx &n, float (&lam)[Q]) {
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     lam[i] = __ldg(lam_in + (size_t)i * plane + n.c);
   });
+}
 
-  const uint32_t dc = ((uint32_t)z * ny + y) * nx + x;
-  float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-  if constexpr (FORCE) {
-    Fx = __ldg(force + dc);
-    Fy = __ldg(force + cells + dc);
-    Fz = __ldg(force + 2 * (size_t)cells + dc);
-  }
-  float dr, jx, jy, jz;
-  shifted_moments(d, dr, jx, jy, jz);
-  const float rho = 1.0f + dr;
+// Shared part of a reverse step at one node, given lambda^{n+1}(x) and the
+// density rho and velocity u = (sum e g + F/2) / rho that the forward
+// collision used there: form mu = J_C^T lambda^{n+1}(x) (which depends on g
+// only through rho and u), scatter it by P^T into lambda_out, and add the
+// force cotangent into gF (GRADF). `sel`: apply the bounce-back rule to the
+// scatter on this node (per-direction address selection).
+template <bool FORCE, bool GRADF>
+__device__ __forceinline__ void adjoint_core(
+    float (&lam)[Q], float *__restrict__ lam_out, float *__restrict__ gF, uint32_t plane,
+    const NodeIdx &n, bool sel, uint32_t dc, uint32_t cells, float rho, float ux, float uy,
+    float uz, float Fx, float Fy, float Fz, float omega, float kf) {
   const float rinv = __frcp_rn(rho);
-  const float ux = fmaf(0.5f, Fx, jx) * rinv;
-  const float uy = fmaf(0.5f, Fy, jy) * rinv;
-  const float uz = fmaf(0.5f, Fz, jz) * rinv;
   const float usq = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
 
   const LamMoments m = lambda_moments(lam);
@@ -161,6 +137,82 @@ __device__ __forceinline__ void adjoint_node(
       lam_out[(size_t)i * plane + source_of<i>(n)] = lam[i];
     });
   }
+}
+
+// One reverse step at node (x, y, z) from the state f^n that entered the
+// forward step: recompute g = P f^n there for rho and u, then adjoint_core.
+// WALLS = false compiles the periodic form only; with WALLS the gather and
+// the scatter apply the bounce-back rule either by per-direction address
+// selection on every node (wall_select) or only on nodes that touch a walled
+// face (a branch, cheaper on long rows).
+template <bool WALLS, bool FORCE, bool GRADF>
+__device__ __forceinline__ void adjoint_node(
+    const float *__restrict__ fn, const float *__restrict__ lam_in,
+    float *__restrict__ lam_out, const float *__restrict__ force, float *__restrict__ gF,
+    int nx, int ny, int nz, int pitch, uint32_t plane, uint32_t walls,
+    const float (&lidc)[Q], float omega, float kf, uint32_t cells, int x, int y, int z,
+    bool wall_select = true) {
+  const NodeIdx n = node_index(nx, ny, nz, pitch, WALLS ? walls : 0u, x, y, z);
+  // bounce-back handled per direction on this node (uniform when selecting)
+  const bool sel = WALLS && (wall_select || on_wall(n));
+
+  // recompute the post-streaming state g = P f^n of the forward step
+  // (measured faster here than a periodic gather plus face fix-ups)
+  float d[Q];
+  if (sel)
+    gather_walled<0>(fn, plane, n, lidc, d);
+  else
+    gather<0>(fn, plane, n, d);
+  float lam[Q];
+  load_lambda(lam_in, plane, n, lam);
+
+  const uint32_t dc = ((uint32_t)z * ny + y) * nx + x;
+  float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+  if constexpr (FORCE) {
+    Fx = __ldg(force + dc);
+    Fy = __ldg(force + cells + dc);
+    Fz = __ldg(force + 2 * (size_t)cells + dc);
+  }
+  // the same FP32 arithmetic as the forward collision, so rho and u are
+  // bit-identical to the ones lbm_step_moments stores
+  float dr, jx, jy, jz;
+  shifted_moments(d, dr, jx, jy, jz);
+  const float rho = 1.0f + dr;
+  const float rinv = __frcp_rn(rho);
+  const float ux = fmaf(0.5f, Fx, jx) * rinv;
+  const float uy = fmaf(0.5f, Fy, jy) * rinv;
+  const float uz = fmaf(0.5f, Fz, jz) * rinv;
+  adjoint_core<FORCE, GRADF>(lam, lam_out, gF, plane, n, sel, dc, cells, rho, ux, uy, uz, Fx,
+                             Fy, Fz, omega, kf);
+}
+
+// One reverse step at node (x, y, z) from the moments rho^n, u^n that the
+// forward step's collision used (dense fields, as lbm_step_moments writes
+// them): no gather of f^n, 16 bytes per node instead of 76.
+template <bool WALLS, bool FORCE, bool GRADF>
+__device__ __forceinline__ void adjoint_node_mom(
+    const float *__restrict__ rho_n, const float *__restrict__ u_n,
+    const float *__restrict__ lam_in, float *__restrict__ lam_out,
+    const float *__restrict__ force, float *__restrict__ gF, int nx, int ny, int nz, int pitch,
+    uint32_t plane, uint32_t walls, float omega, float kf, uint32_t cells, int x, int y, int z,
+    bool wall_select = true) {
+  const NodeIdx n = node_index(nx, ny, nz, pitch, WALLS ? walls : 0u, x, y, z);
+  const bool sel = WALLS && (wall_select || on_wall(n));
+  const uint32_t dc = ((uint32_t)z * ny + y) * nx + x;
+  float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+  if constexpr (FORCE) {
+    Fx = __ldg(force + dc);
+    Fy = __ldg(force + cells + dc);
+    Fz = __ldg(force + 2 * (size_t)cells + dc);
+  }
+  const float rho = __ldg(rho_n + dc);
+  const float ux = __ldg(u_n + dc);
+  const float uy = __ldg(u_n + cells + dc);
+  const float uz = __ldg(u_n + 2 * (size_t)cells + dc);
+  float lam[Q];
+  load_lambda(lam_in, plane, n, lam);
+  adjoint_core<FORCE, GRADF>(lam, lam_out, gF, plane, n, sel, dc, cells, rho, ux, uy, uz, Fx,
+                             Fy, Fz, omega, kf);
 }
 
 // Loss seed at node (x, y, z) of a stored state f_T:

@@ -73,6 +73,11 @@ cudaError_t launch_finalize_sum(const Scratch &scr, int nparts, double offset,
 cudaError_t launch_adjoint_step(const StepArgs &g, const float *lam_in,
                                 float *lam_out, float *grad_force, int bx,
                                 int by, cudaStream_t s);
+// The reverse step from the moments rho^n, u^n of the forward collision
+// (dense FP32 fields) instead of the state f^n.
+cudaError_t launch_adjoint_step_mom(const StepArgs &g, const float *rho_n, const float *u_n,
+                                    const float *lam_in, float *lam_out, float *grad_force,
+                                    int bx, int by, cudaStream_t s);
 cudaError_t launch_adjoint_seed(const StepArgs &g, const float *u_target,
                                 float *lam_out, float *grad_force,
                                 double *partials, cudaStream_t s);
@@ -117,6 +122,11 @@ cudaError_t launch_batch_persistent(const BatchArgs &a, int grid, int threads,
                                     cudaStream_t s);
 cudaError_t launch_batch_step(const BatchArgs &a, const float *fin, float *fout,
                               int threads, cudaStream_t s);
+cudaError_t launch_batch_step_mom(const BatchArgs &a, const float *fin, float *fout, float *rho,
+                                  float *u, int threads, cudaStream_t s);
+cudaError_t launch_batch_adjoint_step_mom(const BatchArgs &a, const float *rho, const float *u,
+                                          const float *lam_in, float *lam_out, float *gF,
+                                          int threads, cudaStream_t s);
 cudaError_t launch_batch_rest(const BatchArgs &a, float *f, int threads, cudaStream_t s);
 cudaError_t launch_batch_moments(const BatchArgs &a, const float *f, float *rho, float *u,
                                  int threads, cudaStream_t s);

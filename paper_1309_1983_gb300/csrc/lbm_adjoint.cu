@@ -7,6 +7,8 @@ namespace lbm {
 
 struct AdjArgs {
   StepArgs g;             // geometry, tau, walls, lid terms, force (fin = f_n)
+  const float *rho_n;     // moments form: rho^n, u^n of the forward collision
+  const float *u_n;
   const float *lam_in;    // lambda^{n+1}, FP32, pitched like f
   float *lam_out;         // lambda^n
   float *grad_force;      // dense [3][cells] accumulated, or null
@@ -35,6 +37,20 @@ __global__ void __launch_bounds__(256, LBM_ADJ_MIN_BLOCKS) k_adjoint_step(const 
                                        g.force, a.grad_force, g.nx, g.ny, g.nz, g.pitch,
                                        g.plane, g.walls, g.lidc, g.omega, g.kf, g.cells, x, y,
                                        z, W == 1);
+}
+
+// The reverse step from stored moments (no gather of f^n): 16 + 152 bytes
+// per node plus the force terms, and no 19-value state in registers.
+template <int W, bool FORCE, bool GRADF>
+__global__ void __launch_bounds__(256) k_adjoint_step_mom(const AdjArgs a) {
+  const StepArgs &g = a.g;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  adjoint_node_mom<(W != 0), FORCE, GRADF>(a.rho_n, a.u_n, a.lam_in, a.lam_out, g.force,
+                                           a.grad_force, g.nx, g.ny, g.nz, g.pitch, g.plane,
+                                           g.walls, g.omega, g.kf, g.cells, x, y, z, W == 1);
 }
 
 // Seed over all nodes (grid stride), FP64 loss partials per block.
@@ -72,6 +88,7 @@ cudaError_t launch_adjoint_step(const StepArgs &g, const float *lam_in,
                                 int by, cudaStream_t s) {
   AdjArgs a;
   a.g = g;
+  a.rho_n = a.u_n = nullptr;
   a.lam_in = lam_in;
   a.lam_out = lam_out;
   a.grad_force = grad_force;
@@ -101,11 +118,48 @@ cudaError_t launch_adjoint_step(const StepArgs &g, const float *lam_in,
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_adjoint_step_mom(const StepArgs &g, const float *rho_n, const float *u_n,
+                                    const float *lam_in, float *lam_out, float *grad_force,
+                                    int bx, int by, cudaStream_t s) {
+  AdjArgs a;
+  a.g = g;
+  a.rho_n = rho_n;
+  a.u_n = u_n;
+  a.lam_in = lam_in;
+  a.lam_out = lam_out;
+  a.grad_force = grad_force;
+  a.u_target = nullptr;
+  a.partials = nullptr;
+  const dim3 grid((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz), blk(bx, by, 1);
+  const int w = g.walls == 0 ? 0 : g.wall_select ? 1 : 2;
+  const bool F = g.force != nullptr, G = grad_force != nullptr;
+#define LBM_ADJ_CASE(W_, F_, G_)                                 \
+  if (w == W_ && F == F_ && G == G_) {                           \
+    k_adjoint_step_mom<W_, F_, G_><<<grid, blk, 0, s>>>(a);      \
+    return cudaGetLastError();                                   \
+  }
+  LBM_ADJ_CASE(0, false, false)
+  LBM_ADJ_CASE(0, false, true)
+  LBM_ADJ_CASE(0, true, false)
+  LBM_ADJ_CASE(0, true, true)
+  LBM_ADJ_CASE(1, false, false)
+  LBM_ADJ_CASE(1, false, true)
+  LBM_ADJ_CASE(1, true, false)
+  LBM_ADJ_CASE(1, true, true)
+  LBM_ADJ_CASE(2, false, false)
+  LBM_ADJ_CASE(2, false, true)
+  LBM_ADJ_CASE(2, true, false)
+  LBM_ADJ_CASE(2, true, true)
+#undef LBM_ADJ_CASE
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_adjoint_seed(const StepArgs &g, const float *u_target,
                                 float *lam_out, float *grad_force,
                                 double *partials, cudaStream_t s) {
   AdjArgs a;
   a.g = g;
+  a.rho_n = a.u_n = nullptr;
   a.lam_in = nullptr;
   a.lam_out = lam_out;
   a.grad_force = grad_force;

@@ -136,6 +136,23 @@ __global__ void __launch_bounds__(256) k_batch_step(const BatchArgs a, const flo
                                            nullptr, nullptr, nullptr, D.cells, x, y, z);
 }
 
+// The same step also writing the collision's rho and u into the dense
+// per-domain fields (rho at coff, u at 3 coff of each domain).
+template <bool WALLS>
+__global__ void __launch_bounds__(256) k_batch_step_mom(const BatchArgs a, const float *fin,
+                                                        float *fout, float *rho, float *u) {
+  const int2 tile = a.tiles[blockIdx.x];
+  const BatchDom &D = a.doms[tile.x];
+  const uint32_t k = (uint32_t)tile.y + threadIdx.x;
+  if (k >= D.cells) return;
+  int x, y, z;
+  decode(D, k, x, y, z);
+  step_node<0, WALLS, false, true, false>(fin + D.foff, fout + D.foff, D.nx, D.ny, D.nz,
+                                          D.pitch, D.plane, D.walls, D.lidc, D.omega, D.kf,
+                                          nullptr, rho + D.coff, u + 3 * (size_t)D.coff,
+                                          D.cells, x, y, z);
+}
+
 // f = w_i (shifted value 0) on every node of every domain.
 __global__ void __launch_bounds__(256) k_batch_rest(const BatchArgs a, float *f) {
   const int2 tile = a.tiles[blockIdx.x];
@@ -229,6 +246,24 @@ __global__ void __launch_bounds__(256, LBM_BATCH_ADJ_MIN_BLOCKS)
                                    x, y, z, true);
 }
 
+// The batched reverse step from stored moments (no gather of f^n).
+template <bool GRADF>
+__global__ void __launch_bounds__(256)
+    k_batch_adjoint_step_mom(const BatchArgs a, const float *rho, const float *u,
+                             const float *lam_in, float *lam_out, float *gF) {
+  const int2 tile = a.tiles[blockIdx.x];
+  const BatchDom &D = a.doms[tile.x];
+  const uint32_t k = (uint32_t)tile.y + threadIdx.x;
+  if (k >= D.cells) return;
+  int x, y, z;
+  decode(D, k, x, y, z);
+  adjoint_node_mom<true, false, GRADF>(rho + D.coff, u + 3 * (size_t)D.coff, lam_in + D.foff,
+                                       lam_out + D.foff, nullptr,
+                                       GRADF ? gF + 3 * (size_t)D.coff : nullptr, D.nx, D.ny,
+                                       D.nz, D.pitch, D.plane, D.walls, D.omega, D.kf, D.cells,
+                                       x, y, z, true);
+}
+
 // Seed per node, FP64 loss partial per tile (block) into partials[tile].
 __global__ void __launch_bounds__(256)
     k_batch_adjoint_seed(const BatchArgs a, const float *fT, const float *ut, float *lam,
@@ -291,6 +326,26 @@ cudaError_t launch_batch_step(const BatchArgs &a, const float *fin, float *fout,
     k_batch_step<true><<<a.ntiles, threads, 0, s>>>(a, fin, fout);
   else
     k_batch_step<false><<<a.ntiles, threads, 0, s>>>(a, fin, fout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_step_mom(const BatchArgs &a, const float *fin, float *fout, float *rho,
+                                  float *u, int threads, cudaStream_t s) {
+  if (a.walls_any)
+    k_batch_step_mom<true><<<a.ntiles, threads, 0, s>>>(a, fin, fout, rho, u);
+  else
+    k_batch_step_mom<false><<<a.ntiles, threads, 0, s>>>(a, fin, fout, rho, u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_adjoint_step_mom(const BatchArgs &a, const float *rho, const float *u,
+                                          const float *lam_in, float *lam_out, float *gF,
+                                          int threads, cudaStream_t s) {
+  if (gF)
+    k_batch_adjoint_step_mom<true><<<a.ntiles, threads, 0, s>>>(a, rho, u, lam_in, lam_out, gF);
+  else
+    k_batch_adjoint_step_mom<false><<<a.ntiles, threads, 0, s>>>(a, rho, u, lam_in, lam_out,
+                                                                 gF);
   return cudaGetLastError();
 }
 

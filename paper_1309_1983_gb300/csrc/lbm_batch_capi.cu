@@ -456,6 +456,17 @@ int lbm_batch_step_to(lbm_batch_t *b, const void *f_in, void *f_out) {
   return LBM_OK;
 }
 
+int lbm_batch_step_to_moments(lbm_batch_t *b, const void *f_in, void *f_out, float *rho,
+                              float *u) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (!f_in || !f_out || f_in == f_out || !rho || !u) return bfail(LBM_EINVAL, "bad buffers");
+  BCUDA(lbm::launch_batch_step_mom(make_args(b), static_cast<const float *>(f_in),
+                                   static_cast<float *>(f_out), rho, u, b->threads, b->stream),
+        "batch step launch");
+  return LBM_OK;
+}
+
 int lbm_batch_adjoint_seed(lbm_batch_t *b, const void *f_T, const float *u_target,
                            float *lambda_T, float *grad_force, double *loss) {
   int rc = check_b(b);
@@ -483,6 +494,19 @@ int lbm_batch_adjoint_step(lbm_batch_t *b, const void *f_n, const float *lambda_
   BCUDA(lbm::launch_batch_adjoint_step(make_args(b), static_cast<const float *>(f_n),
                                        lambda_in, lambda_out, grad_force, b->threads,
                                        b->stream),
+        "batch adjoint step launch");
+  return LBM_OK;
+}
+
+int lbm_batch_adjoint_step_moments(lbm_batch_t *b, const float *rho_n, const float *u_n,
+                                   const float *lambda_in, float *lambda_out,
+                                   float *grad_force) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (!rho_n || !u_n || !lambda_in || !lambda_out || lambda_in == lambda_out)
+    return bfail(LBM_EINVAL, "bad buffers");
+  BCUDA(lbm::launch_batch_adjoint_step_mom(make_args(b), rho_n, u_n, lambda_in, lambda_out,
+                                           grad_force, b->threads, b->stream),
         "batch adjoint step launch");
   return LBM_OK;
 }

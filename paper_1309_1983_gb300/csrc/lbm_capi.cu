@@ -503,6 +503,21 @@ int lbm_step_to(lbm_t *h, const void *f_in, void *f_out) {
   return LBM_OK;
 }
 
+int lbm_step_to_moments(lbm_t *h, const void *f_in, void *f_out, float *rho, float *u) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (!f_in || !f_out || f_in == f_out || !rho || !u) return fail(LBM_EINVAL, "bad buffers");
+  if (!aligned(f_in, 256) || !aligned(f_out, 256))
+    return fail(LBM_EINVAL, "f buffers must be 256-byte aligned");
+  if (!aligned(rho, 4) || !aligned(u, 4)) return fail(LBM_EINVAL, "rho/u misaligned");
+  StepArgs a = make_args(h, f_in, f_out);
+  a.rho = rho;
+  a.u = u;
+  cudaError_t e = launch_one_step(h, true, a);
+  if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+  return LBM_OK;
+}
+
 int lbm_step_push(lbm_t *h, const void *g_in, void *g_out) {
   int rc = check_bound(h);
   if (rc) return rc;
@@ -764,6 +779,23 @@ int lbm_adjoint_step(lbm_t *h, const void *f_n, const float *lambda_in,
   const int abx = h->nx <= 32 ? 32 : 64;
   cudaError_t e = lbm::launch_adjoint_step(g, lambda_in, lambda_out, grad_force, abx,
                                            128 / abx, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint step launch");
+  return LBM_OK;
+}
+
+int lbm_adjoint_step_moments(lbm_t *h, const float *rho_n, const float *u_n,
+                             const float *lambda_in, float *lambda_out, float *grad_force) {
+  int rc = check_bound(h);
+  if (rc) return rc;
+  if (h->storage != lbm::kF32) return fail(LBM_EINVAL, "adjoint needs FP32 storage");
+  if (!rho_n || !u_n || !lambda_in || !lambda_out || lambda_in == lambda_out)
+    return fail(LBM_EINVAL, "bad buffers");
+  StepArgs g = make_args(h, nullptr, nullptr);
+  g.wall_select = h->wall_mode == LBM_WALLS_SELECT ||
+                  (h->wall_mode == LBM_WALLS_AUTO && h->nx < 64);
+  const int abx = h->nx <= 32 ? 32 : 64;
+  cudaError_t e = lbm::launch_adjoint_step_mom(g, rho_n, u_n, lambda_in, lambda_out, grad_force,
+                                               abx, 128 / abx, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint step launch");
   return LBM_OK;
 }

@@ -21,13 +21,17 @@ def bytes_per_update(elem_bytes: int = 4, moments: bool = False, force: bool = F
     return b
 
 
-def adjoint_bytes_per_update(force_grad: bool = True) -> int:
-    """One reverse step of the adjoint kernel: pull f^n (19 FP32 loads),
-    read lambda^{n+1} (19), write lambda^n (19), plus read and write the
-    three force-gradient components."""
-    b = 3 * Q * 4
+def adjoint_bytes_per_update(force_grad: bool = True, moments: bool = False,
+                             force: bool = False) -> int:
+    """One reverse step of the adjoint kernel: read lambda^{n+1} (19 FP32),
+    write lambda^n (19), and either pull f^n (19 FP32 loads) or read the
+    forward collision's rho, u (4 FP32, ``moments``); plus read and write
+    the three force-gradient components and read the force itself."""
+    b = 2 * Q * 4 + (4 * 4 if moments else Q * 4)
     if force_grad:
         b += 2 * 3 * 4
+    if force:
+        b += 3 * 4
     return b
 
 

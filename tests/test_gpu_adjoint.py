@@ -150,6 +150,59 @@ def test_seed_and_u0_gradient_match_oracle(geom):
                                atol=2e-6 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("mode", ["branch", "select"])
+@pytest.mark.parametrize("geom", sorted(GEOMS))
+@pytest.mark.parametrize("shape", [(37, 6, 5), (70, 9, 4)], ids=lambda s: "x".join(map(str, s)))
+def test_moments_form_is_bit_identical(geom, shape, mode):
+    """The reverse step from the forward collision's stored rho, u
+    (lbm_step_to_moments + lbm_adjoint_step_moments) gives the same bits as
+    the step that re-gathers f^n (lbm_adjoint_step)."""
+    from paper_1309_1983_gb300 import capi
+    g = GEOMS[geom]
+    L = _lat(shape, 0.7, g)
+    L.set_wall_mode(mode)
+    OL = _olat(shape, 0.7, g)
+    f = _random_f(OL, 70)
+    L.force.copy_(torch.from_numpy(W.noise((3,) + OL.shape, 71, 2e-3)).float())
+    fd = _to_dev_f(L, f)
+    fout = torch.empty_like(fd)
+    rho = torch.empty(OL.shape, device="cuda")
+    u = torch.empty((3,) + OL.shape, device="cuda")
+    capi.call("lbm_step_to_moments", L.handle, _p(fd), _p(fout), _p(rho), _p(u))
+    lam_in = _lam_to_dev(L, W.noise(f.shape, 72, 1.0))
+    outs = []
+    for fn in ("state", "moments"):
+        lam_out = torch.full_like(lam_in, float("nan"))
+        gF = torch.from_numpy(W.noise((3,) + OL.shape, 73, 0.5)).float().cuda()
+        if fn == "state":
+            capi.call("lbm_adjoint_step", L.handle, _p(fd), _p(lam_in), _p(lam_out), _p(gF))
+        else:
+            capi.call("lbm_adjoint_step_moments", L.handle, _p(rho), _p(u), _p(lam_in),
+                      _p(lam_out), _p(gF))
+        torch.cuda.synchronize()
+        outs.append((_lam_from_dev(L, lam_out), gF.cpu().numpy()))
+    assert np.isfinite(outs[1][0]).all()
+    np.testing.assert_array_equal(outs[1][0], outs[0][0])
+    np.testing.assert_array_equal(outs[1][1], outs[0][1])
+
+
+def test_checkpoint_forms_agree():
+    """The checkpointed driver gives the same bits with segment moments
+    (default) and with re-gathered segment states."""
+    from paper_1309_1983_gb300.adjoint import AdjointProblem
+    nx, ny, nz = 14, 9, 7
+    u0 = torch.from_numpy(W.fourier_modes(nx, ny, nz, 3, 2.0, 0.02)).float().cuda()
+    ut = torch.from_numpy(W.fourier_modes(nx, ny, nz, 4, 2.0, 0.02)).float().cuda()
+    F = torch.from_numpy(W.noise((3, nz, ny, nx), 5, 1e-4)).float().cuda()
+    res = []
+    for moments in (True, False):
+        P = AdjointProblem(nx, ny, nz, 0.7, T=23, K=7, walls=(True, True, True),
+                           lid=(0.05, 0.0, 0.0), moments=moments)
+        res.append([t.cpu().numpy() for t in P.loss_and_grad(u0, F, ut)])
+    for a, b in zip(*res):
+        np.testing.assert_array_equal(a, b)
+
+
 def _rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 

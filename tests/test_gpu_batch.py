@@ -162,3 +162,22 @@ def test_batched_adjoint_matches_oracle_per_domain():
             rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
             assert rel <= 1e-4, (k, rel)
     assert abs(loss.item() - total) <= 1e-4 * total
+
+
+def test_batched_adjoint_forms_agree():
+    """Batched checkpointed adjoint: segment moments (default) and
+    re-gathered segment states give the same bits."""
+    from paper_1309_1983_gb300.adjoint import BatchAdjointProblem
+    from paper_1309_1983_gb300.batch import Batch
+    dims = [(12, 9, 7), (7, 10, 11), (16, 5, 6)]
+    res = []
+    for moments in (True, False):
+        B = Batch(dims, [0.6, 0.75, 0.9], [0.05, 0.03, 0.04])
+        P = BatchAdjointProblem(B, 11, 4, moments=moments)
+        u0 = B.pack_vectors([W.fourier_modes(*d, seed=30 + k, kmax=2.0, amp=0.02)
+                             for k, d in enumerate(dims)])
+        ut = B.pack_vectors([W.fourier_modes(*d, seed=40 + k, kmax=2.0, amp=0.02)
+                             for k, d in enumerate(dims)])
+        res.append([t.cpu().numpy() for t in P.loss_and_grad(u0, torch.zeros_like(u0), ut)])
+    for a, b in zip(*res):
+        np.testing.assert_array_equal(a, b)

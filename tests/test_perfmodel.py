@@ -49,3 +49,13 @@ def test_step_time_spectrum_finds_a_planted_period():
     f, a, res = PM.step_time_spectrum(step)
     assert abs(f - 11.7) <= res and 0.015 < a < 0.025
     assert PM.step_time_spectrum([1.0] * 5) == (None, None, None)
+
+
+def test_adjoint_byte_model():
+    # gathered state: 3 x 76 B of lambda and f plus 24 B of force gradient
+    assert PM.adjoint_bytes_per_update() == 252
+    assert PM.adjoint_bytes_per_update(force=True) == 264
+    assert PM.adjoint_bytes_per_update(force_grad=False) == 228
+    # from stored moments: rho, u (16 B) replace the 76 B gather
+    assert PM.adjoint_bytes_per_update(moments=True, force=True) == 204
+    assert PM.adjoint_bytes_per_update(moments=True) == 192
