@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     p.add_argument("--extras", default="all",
                    help="comma list of secondary workloads: storage,streaming,adjoint,batched,sweep "
-                        "(or all)")
+                        "(or all, the default, for these five) and capacity (1024^3, opt-in)")
     p.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                    help="storage of the main timed workload (profiling runs)")
     p.add_argument("--geometry", default="periodic", choices=["periodic", "cavity"],
@@ -321,6 +321,27 @@ def size_sweep(torch, sizes=(64, 128, 256), steps=1000):
     return out
 
 
+def capacity_workload(torch, n=1024, steps=20):
+    """The largest cubic cavity the benchmark runs on one GPU: 1024^3 nodes,
+    FP32, two f copies = 163 GB of the 288 GB HBM; `steps` single-update
+    launches timed with CUDA events, and the FP64 mass before and after."""
+    from paper_1309_1983_gb300.lattice import Lattice
+    L = Lattice(n, n, n, 0.55, walls=(True, True, True), lid=(0.05, 0.0, 0.0))
+    L.init_equilibrium()
+    m0 = L.mass()
+    L.step(3)
+    ms, per = timed_steps(L, steps, torch)
+    m1 = L.mass()
+    mlups = n ** 3 * steps / (ms / 1e3) / 1e6
+    out = {"config": f"cavity {n}^3 FP32 tau=0.55 lid 0.05", "f_bytes_total": 2 * L.layout.f_bytes,
+           "mlups": round(mlups, 1), "gbs": round(mlups * 152 / 1e3, 1),
+           "mass_rel_drift": abs(m1 - m0) / m0, "steps": steps}
+    L.close()
+    del L
+    torch.cuda.empty_cache()
+    return out
+
+
 def streaming_ablation(torch, n, steps=50):
     """Sec. 4.3 redone on this GPU: streaming alone as an unshifted copy, a
     gather (misaligned reads) and a scatter (misaligned writes), and the full
@@ -573,6 +594,8 @@ def run_ours(args):
         extras = {}
         if "sweep" in want:
             extras["sweep"] = size_sweep(torch)
+        if "capacity" in want:  # opt-in: 163 GB on the device
+            extras["capacity"] = capacity_workload(torch)
         if "storage" in want:
             extras.update(extra_workloads(torch, n))
         if "streaming" in want:
