@@ -168,3 +168,29 @@ def test_16bit_cavity_384_sampled_parity(storage):
         # + 1e-8: the FP32 arithmetic on values near zero (a corner at rest
         # stores exactly 0 where the FP64 reference leaves ~1e-16)
         assert (err <= 1.0001 * _ulp16(ref, storage) + 1e-8).all(), ((x, y, z), err.max())
+
+
+def test_1024_cavity_sampled_parity_and_mass():
+    """The largest cube the benchmark runs (1024^3 nodes, 163 GB of FP32 f):
+    offsets and node indices stay in range, one step matches the oracle on
+    sampled nodes, and mass is conserved. Skipped when the GPU has less
+    than 180 GB free."""
+    from paper_1309_1983_gb300.lattice import Lattice
+    free, _ = torch.cuda.mem_get_info()
+    if free < 180e9:
+        pytest.skip(f"needs 180 GB free device memory, {free / 1e9:.0f} GB free")
+    n, tau, lid = 1024, 0.55, (0.05, 0.0, 0.0)
+    L = Lattice(n, n, n, tau, walls=(True, True, True), lid=lid)
+    try:
+        L.init_equilibrium()
+        m0 = L.mass()
+        L.step(20)
+        assert abs(L.mass() - m0) / m0 < 1e-7
+        w = O.weights()
+        worst = _check_sampled_step(L, (True, True, True), lid, tau, w,
+                                    _samples(n, np.random.default_rng(4), count=24))
+        assert worst <= ATOL_F, worst
+    finally:
+        L.close()
+        del L
+        torch.cuda.empty_cache()
