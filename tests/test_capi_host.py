@@ -4,6 +4,7 @@ any CUDA call."""
 
 import ctypes
 
+import numpy as np
 import pytest
 
 from paper_1309_1983_gb300 import build as B
@@ -139,3 +140,27 @@ def test_lid_needs_lid_flag(lib):
 
 def test_destroy_accepts_null(lib):
     assert lib.lbm_destroy(None) == 0
+
+
+def test_batch_create_validation(lib):
+    def create(ndom, dims, tau, flags=capi.LBM_CAVITY):
+        d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1))
+        t = np.ascontiguousarray(np.asarray(tau, dtype=np.float32).reshape(-1))
+        h = ctypes.c_void_p()
+        rc = lib.lbm_batch_create(ndom, d.ctypes.data_as(ctypes.c_void_p),
+                                  t.ctypes.data_as(ctypes.c_void_p), None, flags,
+                                  ctypes.byref(h))
+        if rc == 0:
+            lib.lbm_batch_destroy(h)
+        else:
+            assert h.value is None
+        return rc
+    assert create(1, [8, 8, 8], [0.6]) == 0
+    assert create(0, [8, 8, 8], [0.6]) == capi.LBM_EINVAL            # no domain
+    assert create(2, [8, 8, 8, 0, 4, 4], [0.6, 0.7]) == capi.LBM_EINVAL  # empty domain
+    assert create(1, [8, 8, 8], [0.5]) == capi.LBM_EINVAL             # tau = 1/2
+    assert create(1, [8, 8, 8], [0.6], capi.LBM_STORE_F16) == capi.LBM_EINVAL
+    assert create(1, [8, 8, 8], [0.6], capi.LBM_LID) == capi.LBM_EINVAL  # lid without z wall
+    assert create(1, [256, 128, 129], [0.6]) == capi.LBM_ERANGE       # > 2^22 nodes
+    many = 257
+    assert create(many, [4, 4, 4] * many, [0.6] * many) == capi.LBM_ERANGE
