@@ -10,6 +10,8 @@ the block's centre with the GPU's f^{n+1} at the node. Sampled nodes include
 every corner, edges, faces and random interior nodes.
 """
 
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -194,3 +196,62 @@ def test_1024_cavity_sampled_parity_and_mass():
         L.close()
         del L
         torch.cuda.empty_cache()
+
+
+def test_adjoint_128_sampled_parity_both_forms():
+    """One reverse step at the adjoint benchmark's size (128^3 periodic,
+    tau = 0.7, with a body force and its gradient), in the default launch:
+    the re-gathering and the stored-moments forms give the same bits over the
+    whole lattice, and sampled nodes match the FP64 oracle's adjoint step run
+    on the 5 x 5 x 5 neighbourhood that determines them (lambda^n at a node
+    takes mu from its neighbours, whose pulled states reach two nodes out)."""
+    from paper_1309_1983_gb300 import capi
+    from paper_1309_1983_gb300.lattice import Lattice
+    n, tau = 128, 0.7
+    L = Lattice(n, n, n, tau, force=True)
+    u0 = torch.from_numpy(W.fourier_modes(n, n, n, seed=1, amp=0.02)).float().cuda()
+    L.force.copy_(torch.from_numpy(W.noise((3, n, n, n), 61, 1e-4)).float())
+    L.init_equilibrium(u=u0)
+    L.step(5)
+    cur, oth = L.current_buffers()
+    fn = cur.clone()
+    gen = torch.Generator(device="cuda").manual_seed(62)
+    lam = torch.rand(L.layout.lambda_bytes // 4, device="cuda", generator=gen) * 2 - 1
+    gF0 = torch.rand((3, n, n, n), device="cuda", generator=gen) - 0.5
+    rho = torch.empty((n, n, n), device="cuda")
+    u = torch.empty((3, n, n, n), device="cuda")
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    capi.call("lbm_step_to_moments", L.handle, P(fn), P(oth), P(rho), P(u))
+    out, gF = [], []
+    for form in ("state", "moments"):
+        lo = torch.full_like(lam, float("nan"))
+        g = gF0.clone()
+        if form == "state":
+            capi.call("lbm_adjoint_step", L.handle, P(fn), P(lam), P(lo), P(g))
+        else:
+            capi.call("lbm_adjoint_step_moments", L.handle, P(rho), P(u), P(lam), P(lo), P(g))
+        out.append(lo)
+        gF.append(g)
+    torch.cuda.synchronize()
+    pitch = L.layout.pitch
+    lam_v = lam.view(19, n, n, pitch)
+    lo_v = out[0].view(19, n, n, pitch)
+    assert torch.isfinite(lo_v[..., :n]).all()
+    assert torch.equal(lo_v[..., :n], out[1].view(19, n, n, pitch)[..., :n])
+    assert torch.equal(gF[0], gF[1])
+    f_v = fn.view(torch.float32).view(19, n, n, pitch)
+    w = O.weights()
+    OL = O.Lattice(5, 5, 5, tau)
+
+    def blk(t, x, y, z):
+        xi, yi, zi = ([(c + d) % n for d in (-2, -1, 0, 1, 2)] for c in (x, y, z))
+        return t[:, zi][:, :, yi][:, :, :, xi].double().cpu().numpy()
+
+    for (x, y, z) in _samples(n, np.random.default_rng(5), count=24):
+        f_blk = blk(f_v, x, y, z) + w[:, None, None, None]
+        ref_g = np.zeros((3, 5, 5, 5))
+        ref = O.adjoint_step(OL, f_blk, blk(lam_v, x, y, z), blk(L.force, x, y, z), ref_g)
+        got = lo_v[:, z, y, x].double().cpu().numpy()
+        assert np.abs(got - ref[:, 2, 2, 2]).max() <= 2e-6 * np.abs(ref).max(), (x, y, z)
+        dg = (gF[0][:, z, y, x] - gF0[:, z, y, x]).double().cpu().numpy()
+        assert np.abs(dg - ref_g[:, 2, 2, 2]).max() <= 2e-6 * np.abs(ref_g).max() + 1e-9, (x, y, z)
