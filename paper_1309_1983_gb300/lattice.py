@@ -162,6 +162,21 @@ class Lattice:
     def step_to(self, f_in, f_out):
         capi.call("lbm_step_to", self._h, _ptr(f_in), _ptr(f_out))
 
+    def step_to_moments(self, f_in, f_out, rho, u):
+        """One step f_in -> f_out also writing the rho, u its collision used
+        (the inputs of the adjoint's stored-moments reverse step)."""
+        capi.call("lbm_step_to_moments", self._h, _ptr(f_in), _ptr(f_out), _ptr(rho), _ptr(u))
+
+    def buffer_bytes(self, which):
+        """Bytes of one caller-owned buffer: "f", "force", "rho", "u",
+        "lambda" or "gradf" (lbm_buffer_bytes)."""
+        k = {"f": capi.LBM_BUF_F, "force": capi.LBM_BUF_FORCE, "rho": capi.LBM_BUF_RHO,
+             "u": capi.LBM_BUF_U, "lambda": capi.LBM_BUF_LAMBDA,
+             "gradf": capi.LBM_BUF_GRADF}[which]
+        b = ctypes.c_size_t()
+        capi.call("lbm_buffer_bytes", self._h, k, ctypes.byref(b))
+        return b.value
+
     def step_push(self, g_in, g_out):
         """One push step (Alg. 2) on post-streaming states."""
         capi.call("lbm_step_push", self._h, _ptr(g_in), _ptr(g_out))
