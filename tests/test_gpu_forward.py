@@ -223,20 +223,22 @@ def test_step_to_matches_step():
     assert torch.equal(out, cur2)
 
 
-@pytest.mark.parametrize("steps", [1, 7])
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("steps", [1, 7, 40])
 @pytest.mark.parametrize("shape", [(24, 24, 24), (19, 7, 2), (33, 5, 17)],
                          ids=lambda s: "x".join(map(str, s)))
-def test_run_host_matches_device_path(steps, shape):
+def test_run_host_matches_device_path(steps, shape, storage):
     """The end-to-end host call (slab-pipelined transfers; single steps
-    interleave the inbound copies, the slab steps and the outbound copies)
-    gives exactly the device path's result."""
+    interleave the inbound copies, the slab steps and the outbound copies;
+    40 steps replay a step graph) gives exactly the device path's result."""
     nx, ny, nz = shape
     u0 = torch.from_numpy(W.fourier_modes(nx, ny, nz, seed=4, kmax=2.0, amp=0.02)).float()
-    L = _lat(nx, ny, nz, 0.8, (0, 1, 1), (0.03, 0, 0))
+    L = _lat(nx, ny, nz, 0.8, (0, 1, 1), (0.03, 0, 0), storage=storage)
     rho_h = torch.empty((nz, ny, nx)).pin_memory()
     u_h = torch.empty((3, nz, ny, nx)).pin_memory()
     L.run_host(u0.pin_memory(), steps, rho_h, u_h)
-    L2 = _lat(nx, ny, nz, 0.8, (0, 1, 1), (0.03, 0, 0))
+    L2 = _lat(nx, ny, nz, 0.8, (0, 1, 1), (0.03, 0, 0), storage=storage)
+    L2.set_graph_steps(0)
     L2.init_equilibrium(u=u0.cuda())
     L2.step(steps)
     rho, u = L2.moments()
