@@ -380,7 +380,8 @@ def streaming_ablation(torch, n, steps=50):
 def adjoint_workload(torch, n=128, T=500, K=50, tau=0.7):
     """Periodic 128^3, tau = 0.7, u0 and u_target random Fourier modes
     (|k| <= 4, amplitude 0.02, seeds 1 and 2), F = 0, T = 500, checkpoints
-    every 50 steps: time of the forward (T steps) and of forward + backward."""
+    every 50 steps: time of the forward (T steps) and of forward + backward,
+    and the gradient's agreement with central differences of the loss."""
     from paper_1309_1983_gb300 import workloads as W
     from paper_1309_1983_gb300.adjoint import AdjointProblem
     P = AdjointProblem(n, n, n, tau, T=T, K=K)
@@ -400,12 +401,26 @@ def adjoint_workload(torch, n=128, T=500, K=50, tau=0.7):
     e[3].synchronize()
     fwd = e[0].elapsed_time(e[1])
     both = e[2].elapsed_time(e[3])
+    # accuracy at this size (untimed): directional derivatives of the GPU
+    # gradient against central differences of the GPU forward loss, along a
+    # third seeded Fourier field for u0 and for F
+    d = torch.from_numpy(W.fourier_modes(n, n, n, seed=3, amp=0.02)).float().cuda()
+    fd_err = {}
+    for name, g, h, args in (("u0", gu0, 1e-2, lambda x: (u0 + x * d, F)),
+                             ("F", gF, 1e-4, lambda x: (u0, F + x * d))):
+        lp = P.loss(*args(h), ut).item()
+        lm = P.loss(*args(-h), ut).item()
+        fdv = (lp - lm) / (2 * h)
+        adv = float((g.double() * d.double()).sum().item())
+        fd_err[name] = abs(fdv - adv) / abs(fdv)
     cells = n ** 3
     out = {"config": f"periodic {n}^3 tau={tau} T={T} K={K}", "forward_ms": round(fwd, 2),
            "forward_backward_ms": round(both, 2), "ratio": round(both / fwd, 3),
            "forward_mlups": round(cells * T / (fwd / 1e3) / 1e6, 1),
+           "reverse_step": "from stored collision moments" if P.moments else "re-gathering f^n",
            "loss": float(loss.item()),
-           "grad_u0_norm": float(gu0.norm().item()), "grad_F_norm": float(gF.norm().item())}
+           "grad_u0_norm": float(gu0.norm().item()), "grad_F_norm": float(gF.norm().item()),
+           "directional_fd_rel_err": fd_err}
     del P
     torch.cuda.empty_cache()
     return out
