@@ -653,7 +653,17 @@ int lbm_run_host(lbm_t *h, const float *u0_host, int n, float *rho_host,
   const size_t nxy = (size_t)h->nx * h->ny;
   const int S = h->nz < lbm_lattice::kMaxSlabs ? h->nz : lbm_lattice::kMaxSlabs;
   int zs[lbm_lattice::kMaxSlabs + 1];
-  for (int k = 0; k <= S; ++k) zs[k] = (int)((long long)k * h->nz / S);
+  // Slabs 0..2 thin: the first outbound copy (slab 1) waits for them to be
+  // copied in and initialised, and slab 0 is the last one out, so thin
+  // leading slabs shorten the start and the tail of the pipeline.
+  const int thin = S >= 8 ? h->nz / (4 * S) : 0;
+  if (thin >= 1 && h->nz - 3 * thin >= S - 3) {
+    for (int k = 0; k <= 3; ++k) zs[k] = k * thin;
+    for (int k = 4; k <= S; ++k)
+      zs[k] = 3 * thin + (int)((long long)(k - 3) * (h->nz - 3 * thin) / (S - 3));
+  } else {
+    for (int k = 0; k <= S; ++k) zs[k] = (int)((long long)k * h->nz / S);
+  }
   float *u0d = h->stage;            // 3 * cells
   float *rd = h->stage + 3 * cells;  // cells
   float *ud = rd + cells;            // 3 * cells

@@ -59,3 +59,14 @@ def test_adjoint_byte_model():
     # from stored moments: rho, u (16 B) replace the 76 B gather
     assert PM.adjoint_bytes_per_update(moments=True, force=True) == 204
     assert PM.adjoint_bytes_per_update(moments=True) == 192
+
+
+def test_validation_scalings_follow_eq8():
+    from paper_1309_1983_gb300 import validation as V
+    for N, Re in ((24, 100.0), (128, 400.0), (256, 1000.0)):
+        tau = V.tau_for(N, 0.05, Re)
+        assert abs(PM.reynolds(0.05, tau, N) - Re) < 1e-9 * Re
+        U = V.lid_for(N, 0.53, Re)
+        assert abs(PM.reynolds(U, 0.53, N) - Re) < 1e-9 * Re
+    # diffusive scaling: doubling N halves the lid speed at fixed tau
+    assert abs(V.lid_for(64, 0.6, 100) - 2 * V.lid_for(128, 0.6, 100)) < 1e-15
