@@ -83,15 +83,12 @@ __global__ void __launch_bounds__(kReduceThreads)
   bool bad = false;
   const uint32_t plane_nodes = (uint32_t)a.nx * a.ny;
   const uint32_t dc_end = (uint32_t)(a.z0 + a.zn) * plane_nodes;
-  const uint32_t nx = a.nx, ny = a.ny;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  uint32_t dc = (uint32_t)a.z0 * plane_nodes + blockIdx.x * blockDim.x + threadIdx.x;
-  // (x, y, z) of dc, then advanced by the grid stride with carries: the
-  // divisions run once per thread, not once per node
-  uint32_t x = dc % nx, y = (dc / nx) % ny, z = dc / plane_nodes;
-  const uint32_t sx = stride % nx, sy = (stride / nx) % ny, sz = stride / plane_nodes;
-  for (; dc < dc_end; dc += stride) {
-    const uint32_t c = (z * ny + y) * a.pitch + x;
+  for (uint32_t dc = (uint32_t)a.z0 * plane_nodes + blockIdx.x * blockDim.x + threadIdx.x;
+       dc < dc_end; dc += gridDim.x * blockDim.x) {
+    const uint32_t x = dc % a.nx;
+    const uint32_t t = dc / a.nx;
+    const uint32_t y = t % a.ny, z = t / a.ny;
+    const uint32_t c = (z * a.ny + y) * a.pitch + x;
     float d[Q];
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
@@ -114,13 +111,6 @@ __global__ void __launch_bounds__(kReduceThreads)
     }
     acc += (double)dr;
     bad |= !isfinite(r);
-    x += sx;
-    uint32_t carry = x >= nx;
-    x -= carry ? nx : 0u;
-    y += sy + carry;
-    carry = y >= ny;
-    y -= carry ? ny : 0u;
-    z += sz + carry;
   }
   if (!partials) return;
   // block reduction of acc (warp shuffles, then one warp over the warps)
