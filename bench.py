@@ -30,6 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_DEFAULT = 384
+# lattice updates per second; the HBM-roofline fraction is in "roofline" and
+# the adjoint/forward time ratio with its accuracy in extras.adjoint
+METRIC = "D3Q19 MLUPS"
 TAU = 0.8
 AMP = 0.01
 FALLBACK_HBM_GBS = 6800.0
@@ -218,7 +221,7 @@ def run_reference(args):
               f"{args.steps} steps in one oracle call (bounded sample of the {args.n}^3 "
               f"workload; same per-node arithmetic)")
     line = {
-        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -634,7 +637,7 @@ def run_ours(args):
                           f"arithmetic as the {n}^3 workload")}
 
     line = {
-        "metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
