@@ -143,9 +143,9 @@ int lbm_set_block(lbm_t *h, int bx, int by);
 /* Step kernel variant. LBM_KERNEL_NODE: one node per thread (every storage
  * type). LBM_KERNEL_PAIR: 16-bit storage only; two x-adjacent nodes per
  * thread with 32-bit packed loads and stores and warp shuffles for the
- * x-shifted pulls; bit-identical results. Default: NODE (on GB300 the pair
- * kernel's shuffles and register cost made it slower, like the shuffle
- * propagation the paper measured on Kepler, Sec. 4.3.2). */
+ * x-shifted pulls; bit-identical results (slower on GB300, like the shuffle
+ * propagation the paper measured on Kepler, Sec. 4.3.2). Default: NODE for
+ * FP32, LBM_KERNEL_X2 (below) for 16-bit storage. */
 #define LBM_KERNEL_NODE 0
 #define LBM_KERNEL_PAIR 1
 /* LBM_KERNEL_BULK / BULK1: the pulled rows are staged in shared memory by
@@ -153,6 +153,12 @@ int lbm_set_block(lbm_t *h, int bx, int by);
  * 1-row tiles); bit-identical results; lbm_step_moments still uses NODE. */
 #define LBM_KERNEL_BULK 2
 #define LBM_KERNEL_BULK1 3
+/* LBM_KERNEL_X2: 16-bit storage only; two x-adjacent nodes per thread and no
+ * exchange between threads: one aligned 32-bit load per pair for the 9
+ * directions with e_x = 0, two 16-bit loads for the others, one packed
+ * 32-bit store per direction, two-value conversions; bit-identical results.
+ * Block shape: lbm_set_pair_block. */
+#define LBM_KERNEL_X2 4
 int lbm_set_kernel(lbm_t *h, int variant);
 
 /* How the one-node kernel applies bounce-back: LBM_WALLS_SELECT picks each
@@ -160,9 +166,9 @@ int lbm_set_kernel(lbm_t *h, int variant);
  * node) for every node, with no divergence; LBM_WALLS_BRANCH gathers as if
  * periodic and re-reads the bounced directions only on wall nodes (fewer
  * instructions when wall nodes are rare in each warp). LBM_WALLS_AUTO
- * (default) selects for FP32 storage and for rows shorter than 256 nodes,
- * else branches. The results are identical. Returns LBM_EINVAL for any
- * other mode. */
+ * (default) selects for FP32 storage, for the LBM_KERNEL_X2 kernel and for
+ * rows shorter than 256 nodes, else branches. The results are identical.
+ * Returns LBM_EINVAL for any other mode. */
 #define LBM_WALLS_AUTO 0
 #define LBM_WALLS_BRANCH 1
 #define LBM_WALLS_SELECT 2

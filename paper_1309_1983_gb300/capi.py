@@ -46,6 +46,7 @@ LBM_KERNEL_NODE = 0
 LBM_KERNEL_PAIR = 1
 LBM_KERNEL_BULK = 2
 LBM_KERNEL_BULK1 = 3
+LBM_KERNEL_X2 = 4
 
 
 class LBMError(RuntimeError):

@@ -46,6 +46,10 @@ cudaError_t launch_step(int storage, bool moments, const StepArgs &a, int bx,
                         int by, cudaStream_t s);
 // 16-bit storage, two x-adjacent nodes per thread (bxp pairs per block row,
 // a multiple of 32).
+// 16-bit storage, two x-adjacent nodes per thread without exchange between
+// threads (bxp pairs per block row, `by` rows).
+cudaError_t launch_step_x2(int storage, bool moments, const StepArgs &a, int bxp, int by,
+                           cudaStream_t s);
 cudaError_t launch_step_pair16(int storage, bool moments, const StepArgs &a, int bxp, int by,
                                cudaStream_t s);
 // Bulk-copy (TMA) staged step, persistent over tiles; variant 0: 2-row tiles,

@@ -58,12 +58,13 @@ StepArgs make_args(const lbm_t *h, const void *fin, void *fout) {
   a.walls = h->flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z);
   a.z0 = 0;
   a.zn = h->nz;
-  // 16-bit storage is issue-bound: there the branch form's shorter common
-  // path wins once wall nodes are rare in every warp (long rows); FP32 is
-  // bandwidth-bound and the divergence-free select form is never slower
+  // The one-node kernel with 16-bit storage is issue-bound: there the branch
+  // form's shorter common path wins once wall nodes are rare in every warp
+  // (long rows). FP32 is bandwidth-bound and the divergence-free select form
+  // is never slower; the two-node 16-bit kernel is fastest with it too.
   a.wall_select = h->wall_mode == LBM_WALLS_SELECT ||
                   (h->wall_mode == LBM_WALLS_AUTO &&
-                   (h->storage == lbm::kF32 || h->nx < 256));
+                   (h->storage == lbm::kF32 || h->nx < 256 || h->kernel == LBM_KERNEL_X2));
   for (int i = 0; i < lbm::Q; ++i) {
     a.lidc[i] = 0.0f;
     if ((h->flags & LBM_LID) && lbm::kEz[i] == -1)
@@ -111,6 +112,8 @@ int ensure_scratch(lbm_t *h) {
 cudaError_t launch_one_step(const lbm_t *h, bool mom, const StepArgs &a, cudaStream_t s) {
   if (h->kernel == LBM_KERNEL_PAIR && h->storage != lbm::kF32)
     return lbm::launch_step_pair16(h->storage, mom, a, h->pbx, h->pby, s);
+  if (h->kernel == LBM_KERNEL_X2 && h->storage != lbm::kF32)
+    return lbm::launch_step_x2(h->storage, mom, a, h->pbx, h->pby, s);
   if ((h->kernel == LBM_KERNEL_BULK || h->kernel == LBM_KERNEL_BULK1) && !mom)
     return lbm::launch_step_bulk(h->storage, a, h->scr.err,
                                  h->kernel == LBM_KERNEL_BULK1 ? 1 : 0, h->sms, s);
@@ -313,7 +316,9 @@ int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
   if (by > ny) by = ny;
   h->bx = bx;
   h->by = by < 1 ? 1 : by;
-  h->kernel = LBM_KERNEL_NODE;  // the pair kernel measured slower on GB300
+  // 16-bit storage: two nodes per thread (fewer instructions per node where
+  // the one-node kernel is issue-bound); FP32: one node per thread
+  h->kernel = storage == lbm::kF32 ? LBM_KERNEL_NODE : LBM_KERNEL_X2;
   h->wall_mode = LBM_WALLS_AUTO;
   h->pbx = 64;
   h->pby = ny < 4 ? ny : 4;
@@ -424,10 +429,10 @@ int lbm_set_block(lbm_t *h, int bx, int by) {
 int lbm_set_kernel(lbm_t *h, int variant) {
   if (!h) return fail(LBM_EINVAL, "NULL handle");
   if (variant != LBM_KERNEL_NODE && variant != LBM_KERNEL_PAIR && variant != LBM_KERNEL_BULK &&
-      variant != LBM_KERNEL_BULK1)
+      variant != LBM_KERNEL_BULK1 && variant != LBM_KERNEL_X2)
     return fail(LBM_EINVAL, "unknown kernel variant");
-  if (variant == LBM_KERNEL_PAIR && h->storage == lbm::kF32)
-    return fail(LBM_EINVAL, "the pair kernel needs 16-bit storage");
+  if ((variant == LBM_KERNEL_PAIR || variant == LBM_KERNEL_X2) && h->storage == lbm::kF32)
+    return fail(LBM_EINVAL, "the pair kernels need 16-bit storage");
   h->kernel = variant;
   h->config_version++;
   return LBM_OK;

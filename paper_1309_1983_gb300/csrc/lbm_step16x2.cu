@@ -1,0 +1,194 @@
+// lbm_step16x2.cu - the fused step (Alg. 3) for 16-bit storage with two
+// x-adjacent nodes (x0, x0 + 1), x0 even, per thread and no data exchange
+// between threads.
+//
+// With 16-bit values the one-node kernel is bound by instruction issue, not
+// by DRAM: half the bytes per node means twice the nodes per second, and
+// every node still pays 19 load and 19 store instructions, their addresses
+// and 38 conversions. Here the two nodes of a pair share them where the
+// layout allows:
+//   * the 9 directions with e_x = 0 pull (x0 - 0, x0 + 1 - 0) from the same
+//     row: one aligned 32-bit load per pair, unpacked by one conversion per
+//     half;
+//   * the 10 directions with e_x != 0 pull from x0 - e_x and x0 + 1 - e_x,
+//     an odd offset: two 16-bit loads (the misaligned-read variant of
+//     Sec. 4.3.2, as in the one-node kernel);
+//   * all 19 results are stored as one aligned 32-bit word per pair, packed
+//     by one two-value conversion.
+// The arithmetic per node is that of the one-node kernel (same collision,
+// same round-to-nearest-even conversions), so both produce identical bits.
+// On an odd-length row the last pair's second node lies in the row padding
+// (the pitch is a multiple of 16 values): it is loaded and stored but never
+// used.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "d3q19.cuh"
+#include "internal.h"
+#include "stream.cuh"
+
+namespace lbm {
+
+template <int S>
+struct Pack16;
+
+template <>
+struct Pack16<1> {
+  static __device__ __forceinline__ float2 unpack(uint32_t v) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(&v));
+  }
+  static __device__ __forceinline__ uint32_t pack(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+  }
+};
+
+template <>
+struct Pack16<2> {
+  static __device__ __forceinline__ float2 unpack(uint32_t v) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v));
+  }
+  static __device__ __forceinline__ uint32_t pack(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+  }
+};
+
+// Pulled values of both nodes for direction i (bounce-back by address
+// selection when SEL; the e_x = 0 pulls of the pair share y, z, hence their
+// wall decisions, so they stay one 32-bit load).
+template <int S, bool SEL, int i>
+__device__ __forceinline__ void pull_pair(const typename Store<S>::T *__restrict__ fin,
+                                          uint32_t plane, const NodeIdx &n0, const NodeIdx &n1,
+                                          const float (&lidc)[Q], float &v0, float &v1) {
+  using T = typename Store<S>::T;
+  if constexpr (kEx[i] == 0) {
+    size_t idx = (size_t)i * plane + source_of<i>(n0);
+    if constexpr (SEL) {
+      if (bounces<i>(n0)) idx = (size_t)kOpp_v<i> * plane + n0.c;
+    }
+    const float2 p = Pack16<S>::unpack(__ldg(reinterpret_cast<const unsigned int *>(fin + idx)));
+    v0 = p.x;
+    v1 = p.y;
+  } else {
+    size_t i0 = (size_t)i * plane + source_of<i>(n0);
+    size_t i1 = (size_t)i * plane + source_of<i>(n1);
+    if constexpr (SEL) {
+      if (bounces<i>(n0)) i0 = (size_t)kOpp_v<i> * plane + n0.c;
+      if (bounces<i>(n1)) i1 = (size_t)kOpp_v<i> * plane + n1.c;
+    }
+    v0 = Store<S>::ld(fin + i0);
+    v1 = Store<S>::ld(fin + i1);
+  }
+  if constexpr (SEL && kEz[i] == -1) {  // the moving plane z = nz (z1 implies a bounce)
+    v0 += n0.z1 ? lidc[i] : 0.0f;
+    v1 += n1.z1 ? lidc[i] : 0.0f;
+  }
+}
+
+// Launch bounds: by default only the block size is fixed (64 registers for
+// the periodic kernel, 74-80 with walls); LBM_X2_MIN_BLOCKS asks for that
+// many resident 256-thread blocks per SM instead (tuning experiments).
+#ifdef LBM_X2_MIN_BLOCKS
+#define LBM_X2_BOUNDS __launch_bounds__(256, LBM_X2_MIN_BLOCKS)
+#else
+#define LBM_X2_BOUNDS __launch_bounds__(256)
+#endif
+
+// W: 0 periodic, 1 walls by address selection, 2 walls by the wall-node
+// branch (the one-node kernel's face fix-ups, per node of the pair).
+template <int S, int W, bool FORCE, bool MOM>
+__global__ void LBM_X2_BOUNDS k_step_x2(const StepArgs a) {
+  using T = typename Store<S>::T;
+  const int x0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = a.z0 + blockIdx.z;
+  if (x0 >= a.nx || y >= a.ny) return;
+  const bool has1 = x0 + 1 < a.nx;
+  const T *__restrict__ fin = static_cast<const T *>(a.fin);
+  T *__restrict__ fout = static_cast<T *>(a.fout);
+  const uint32_t walls = W != 0 ? a.walls : 0u;
+  const NodeIdx n0 = node_index(a.nx, a.ny, a.nz, a.pitch, walls, x0, y, z);
+  // the padding node of an odd row pulls what node 0 pulls (in bounds, unused)
+  const NodeIdx n1 = node_index(a.nx, a.ny, a.nz, a.pitch, walls, has1 ? x0 + 1 : x0, y, z);
+
+  float d0[Q], d1[Q];
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    pull_pair<S, W == 1, i>(fin, a.plane, n0, n1, a.lidc, d0[i], d1[i]);
+  });
+  if constexpr (W == 2) {
+    bounce_fixup<S>(fin, a.plane, n0, a.lidc, d0);
+    if (has1) bounce_fixup<S>(fin, a.plane, n1, a.lidc, d1);
+  }
+  const uint32_t dc = ((uint32_t)z * a.ny + y) * a.nx + x0;
+  float F0x = 0.f, F0y = 0.f, F0z = 0.f, F1x = 0.f, F1y = 0.f, F1z = 0.f;
+  if constexpr (FORCE) {
+    F0x = __ldg(a.force + dc);
+    F0y = __ldg(a.force + a.cells + dc);
+    F0z = __ldg(a.force + 2 * (size_t)a.cells + dc);
+    if (has1) {
+      F1x = __ldg(a.force + dc + 1);
+      F1y = __ldg(a.force + a.cells + dc + 1);
+      F1z = __ldg(a.force + 2 * (size_t)a.cells + dc + 1);
+    }
+  }
+  float r0, u0x, u0y, u0z, r1, u1x, u1y, u1z;
+  collide<FORCE>(d0, a.omega, a.kf, F0x, F0y, F0z, r0, u0x, u0y, u0z);
+  collide<FORCE>(d1, a.omega, a.kf, F1x, F1y, F1z, r1, u1x, u1y, u1z);
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    __stcs(reinterpret_cast<unsigned int *>(fout + (size_t)i * a.plane + n0.c),
+           Pack16<S>::pack(d0[i], d1[i]));
+  });
+  if constexpr (MOM) {
+    a.rho[dc] = r0;
+    a.u[dc] = u0x;
+    a.u[a.cells + dc] = u0y;
+    a.u[2 * (size_t)a.cells + dc] = u0z;
+    if (has1) {
+      a.rho[dc + 1] = r1;
+      a.u[dc + 1] = u1x;
+      a.u[a.cells + dc + 1] = u1y;
+      a.u[2 * (size_t)a.cells + dc + 1] = u1z;
+    }
+  }
+}
+
+template <int S>
+static void x2_dispatch(bool moments, const StepArgs &a, dim3 g, dim3 b, cudaStream_t s) {
+  const int walls = a.walls == 0 ? 0 : a.wall_select ? 1 : 2;
+  const bool force = a.force != nullptr;
+#define LBM_X2_CASE(W, F, M)                                    \
+  if (walls == W && force == F && moments == M) {               \
+    k_step_x2<S, W, F, M><<<g, b, 0, s>>>(a);                   \
+    return;                                                     \
+  }
+  LBM_X2_CASE(0, false, false)
+  LBM_X2_CASE(0, false, true)
+  LBM_X2_CASE(0, true, false)
+  LBM_X2_CASE(0, true, true)
+  LBM_X2_CASE(1, false, false)
+  LBM_X2_CASE(1, false, true)
+  LBM_X2_CASE(1, true, false)
+  LBM_X2_CASE(1, true, true)
+  LBM_X2_CASE(2, false, false)
+  LBM_X2_CASE(2, false, true)
+  LBM_X2_CASE(2, true, false)
+  LBM_X2_CASE(2, true, true)
+#undef LBM_X2_CASE
+}
+
+cudaError_t launch_step_x2(int storage, bool moments, const StepArgs &a, int bxp, int by,
+                           cudaStream_t s) {
+  const int pairs = (a.nx + 1) / 2;
+  const dim3 g((pairs + bxp - 1) / bxp, (a.ny + by - 1) / by, a.zn), b(bxp, by, 1);
+  switch (storage) {
+    case kF16: x2_dispatch<1>(moments, a, g, b, s); break;
+    case kBF16: x2_dispatch<2>(moments, a, g, b, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -92,15 +92,18 @@ PAIR_GEOMS = {
 }
 
 
+@pytest.mark.parametrize("variant,mode", [("pair", "auto"), ("x2", "select"), ("x2", "branch")])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 @pytest.mark.parametrize("geom", sorted(PAIR_GEOMS))
 @pytest.mark.parametrize("shape", PAIR_SHAPES, ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("force", [False, True])
-def test_pair_kernel_is_bit_identical_to_node_kernel(storage, geom, shape, force):
-    """The two-nodes-per-thread kernel (packed 32-bit pulls, warp shuffles for
-    the x-shifted directions) computes the same bits as the one-node kernel,
-    including odd and short rows, every wall combination, the lid, a body
-    force and the fused moment output."""
+def test_pair_kernel_is_bit_identical_to_node_kernel(storage, geom, shape, force, variant, mode):
+    """The two-nodes-per-thread kernels ("pair": packed 32-bit pulls and warp
+    shuffles for the x-shifted directions; "x2": packed loads for e_x = 0,
+    16-bit loads otherwise, no exchange between threads, in both wall forms)
+    compute the same bits as the one-node kernel, including odd and short
+    rows, every wall combination, the lid, a body force and the fused moment
+    output."""
     from paper_1309_1983_gb300.lattice import Lattice
     nx, ny, nz = shape
     g = PAIR_GEOMS[geom]
@@ -110,10 +113,11 @@ def test_pair_kernel_is_bit_identical_to_node_kernel(storage, geom, shape, force
     f0 = f0 * (1 + W.noise(f0.shape, 3, 0.1))
     F = torch.from_numpy(W.noise((3,) + OL.shape, 4, 1e-3)).float()
     outs = []
-    for variant in ("node", "pair"):
+    for kern in ("node", variant):
         L = Lattice(nx, ny, nz, 0.6, walls=g["walls"], lid=g["lid"], storage=storage,
                     force=force)
-        L.set_kernel(variant)
+        L.set_kernel(kern)
+        L.set_wall_mode(mode)
         if force:
             L.force.copy_(F)
         L.set_f(f0)
@@ -124,10 +128,12 @@ def test_pair_kernel_is_bit_identical_to_node_kernel(storage, geom, shape, force
     assert torch.equal(outs[0][1], outs[1][1]) and torch.equal(outs[0][2], outs[1][2])
 
 
+@pytest.mark.parametrize("variant", ["pair", "x2"])
 @pytest.mark.parametrize("block", [(32, 1), (32, 8), (64, 4), (128, 2), (256, 1)])
-def test_pair_block_shapes_agree(block):
+def test_pair_block_shapes_agree(block, variant):
     from paper_1309_1983_gb300.lattice import Lattice
     L = Lattice(150, 13, 5, 0.7, walls=(True, True, True), lid=(0.05, 0, 0), storage="f16")
+    L.set_kernel(variant)
     L.init_equilibrium()
     L.step(4)
     ref = L.get_f()
