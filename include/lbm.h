@@ -185,7 +185,8 @@ int lbm_set_wall_mode(lbm_t *h, int mode);
 int lbm_set_graph_steps(lbm_t *h, int steps);
 
 /* Block shape of the pair kernel: bxp pairs along x (a multiple of 32) by
- * `by` rows, bxp * by <= 256. Default: 64 x 4 (or fewer rows for small ny). */
+ * `by` rows, bxp * by <= 256, used by LBM_KERNEL_PAIR and LBM_KERNEL_X2.
+ * Default: 64 x 2 (1 row when ny = 1). */
 int lbm_set_pair_block(lbm_t *h, int bxp, int by);
 
 /* Launch-shape autotuner (no counterpart in the paper, which fixed its block

@@ -320,8 +320,8 @@ int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
   // the one-node kernel is issue-bound); FP32: one node per thread
   h->kernel = storage == lbm::kF32 ? LBM_KERNEL_NODE : LBM_KERNEL_X2;
   h->wall_mode = LBM_WALLS_AUTO;
-  h->pbx = 64;
-  h->pby = ny < 4 ? ny : 4;
+  h->pbx = 64;  // 64 pairs x 2 rows measured best for the two-node kernel
+  h->pby = ny < 2 ? ny : 2;
   h->device = -1;
   h->stage = nullptr;
   h->pipe_ready = false;
