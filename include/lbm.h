@@ -333,7 +333,7 @@ int lbm_adjoint_seed(lbm_t *h, const void *f_T, const float *u_target,
  * written exactly once (the transposed pull is a permutation). Launch: 64 x 2
  * blocks (32 x 4 for rows of 32 nodes or fewer); walls by address selection when
  * the wall mode is LBM_WALLS_SELECT, or LBM_WALLS_AUTO with rows shorter than
- * 64 nodes, else by a branch on wall nodes. */
+ * 64 nodes, else only in the warps that hold a wall node (a warp vote). */
 int lbm_adjoint_step(lbm_t *h, const void *f_n, const float *lambda_in,
                      float *lambda_out, float *grad_force);
 

@@ -66,6 +66,14 @@ __device__ __forceinline__ void mat_vec(const float (&L2)[6], float vx, float vy
   oz = fmaf(L2[4], vx, fmaf(L2[5], vy, L2[2] * vz));
 }
 
+// Whether any active thread of the warp holds a wall node: in the branch
+// form the whole warp then takes the bounce-back path (selecting per
+// direction, correct for every node), so warps never split between the two
+// paths. Called by all active threads of the warp at the same point.
+__device__ __forceinline__ bool warp_has_wall(const NodeIdx &n) {
+  return __any_sync(__activemask(), on_wall(n));
+}
+
 // lambda^{n+1} at the node (aligned loads).
 __device__ __forceinline__ void load_lambda(const float *__restrict__ lam_in, uint32_t plane,
                                             const NodeIdx &n, float (&lam)[Q]) {
@@ -143,8 +151,8 @@ __device__ __forceinline__ void adjoint_core(
 // forward step: recompute g = P f^n there for rho and u, then adjoint_core.
 // WALLS = false compiles the periodic form only; with WALLS the gather and
 // the scatter apply the bounce-back rule either by per-direction address
-// selection on every node (wall_select) or only on nodes that touch a walled
-// face (a branch, cheaper on long rows).
+// selection on every node (wall_select) or only in the warps that hold a
+// node on a walled face (cheaper on long rows).
 template <bool WALLS, bool FORCE, bool GRADF>
 __device__ __forceinline__ void adjoint_node(
     const float *__restrict__ fn, const float *__restrict__ lam_in,
@@ -153,8 +161,7 @@ __device__ __forceinline__ void adjoint_node(
     const float (&lidc)[Q], float omega, float kf, uint32_t cells, int x, int y, int z,
     bool wall_select = true) {
   const NodeIdx n = node_index(nx, ny, nz, pitch, WALLS ? walls : 0u, x, y, z);
-  // bounce-back handled per direction on this node (uniform when selecting)
-  const bool sel = WALLS && (wall_select || on_wall(n));
+  const bool sel = WALLS && (wall_select || warp_has_wall(n));
 
   // recompute the post-streaming state g = P f^n of the forward step
   // (measured faster here than a periodic gather plus face fix-ups)
@@ -197,7 +204,7 @@ __device__ __forceinline__ void adjoint_node_mom(
     uint32_t plane, uint32_t walls, float omega, float kf, uint32_t cells, int x, int y, int z,
     bool wall_select = true) {
   const NodeIdx n = node_index(nx, ny, nz, pitch, WALLS ? walls : 0u, x, y, z);
-  const bool sel = WALLS && (wall_select || on_wall(n));
+  const bool sel = WALLS && (wall_select || warp_has_wall(n));
   const uint32_t dc = ((uint32_t)z * ny + y) * nx + x;
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
   if constexpr (FORCE) {
