@@ -28,8 +28,10 @@
  *     code; lbm_strerror() names it. No exception or abort crosses the ABI.
  *   - Handles are opaque. Device buffers are owned by the caller (for
  *     example torch tensors passed as raw pointers); the library never frees
- *     them. A handle allocates only a small device scratch area (error word,
- *     reduction partials) on first bind, released by lbm_destroy.
+ *     them. A handle allocates a small device scratch area (error word,
+ *     reduction partials) on first bind, staging of 28 bytes per node on the
+ *     first lbm_run_host, and a private stream with CUDA graphs on the first
+ *     multi-step call; lbm_destroy releases all of them.
  *   - Work is enqueued on the bound CUDA stream and is asynchronous, except
  *     where a call returns a host value (documented per call), which
  *     synchronises that stream.
@@ -37,7 +39,9 @@
  *     lbm_get_layout: Structure of Arrays [19][nz][ny][pitch] (Sec. 4.1),
  *     x fastest, each x row padded to `pitch` elements (32-byte aligned
  *     rows), element type FP32, FP16 or BF16 per LBM_STORE_*, holding the
- *     SHIFTED value f_i - w_i. Padding elements are never read.
+ *     SHIFTED value f_i - w_i. Padding elements never enter the result (the
+ *     two-node 16-bit kernels load and store the padding element of an odd
+ *     row together with the row's last node).
  *   - Field buffers (rho, velocity u, force F, targets, gradients) are dense
  *     FP32 planes without padding: scalars [nz][ny][nx], vectors
  *     [3][nz][ny][nx] (component-major).
