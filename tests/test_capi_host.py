@@ -164,3 +164,31 @@ def test_batch_create_validation(lib):
     assert create(1, [256, 128, 129], [0.6]) == capi.LBM_ERANGE       # > 2^22 nodes
     many = 257
     assert create(many, [4, 4, 4] * many, [0.6] * many) == capi.LBM_ERANGE
+
+
+def test_moments_form_entry_points_validate(lib):
+    nul = ctypes.c_void_p()
+    assert lib.lbm_step_to_moments(None, nul, nul, nul, nul) == capi.LBM_EINVAL
+    assert lib.lbm_adjoint_step_moments(None, nul, nul, nul, nul, nul) == capi.LBM_EINVAL
+    assert lib.lbm_batch_step_to_moments(None, nul, nul, nul, nul) == capi.LBM_EINVAL
+    assert lib.lbm_batch_adjoint_step_moments(None, nul, nul, nul, nul, nul) == capi.LBM_EINVAL
+    h = capi.create(8, 8, 8, 0.8, 0)
+    try:
+        assert lib.lbm_step_to_moments(h, nul, nul, nul, nul) == capi.LBM_EUNBOUND
+        assert lib.lbm_adjoint_step_moments(h, nul, nul, nul, nul, nul) == capi.LBM_EUNBOUND
+    finally:
+        lib.lbm_destroy(h)
+
+
+def test_kernel_variants_need_matching_storage(lib):
+    h32 = capi.create(8, 8, 8, 0.8, capi.LBM_STORE_F32)
+    h16 = capi.create(8, 8, 8, 0.8, capi.LBM_STORE_F16)
+    try:
+        for v in (capi.LBM_KERNEL_PAIR, capi.LBM_KERNEL_X2):
+            assert lib.lbm_set_kernel(h32, v) == capi.LBM_EINVAL
+            assert lib.lbm_set_kernel(h16, v) == 0
+        assert lib.lbm_set_kernel(h16, 5) == capi.LBM_EINVAL
+        assert lib.lbm_set_kernel(h32, capi.LBM_KERNEL_NODE) == 0
+    finally:
+        lib.lbm_destroy(h32)
+        lib.lbm_destroy(h16)
