@@ -82,7 +82,7 @@ def measured_hbm():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_1309_1983_gb300/csrc/lbm_step.cu", "paper_1309_1983_gb300/csrc/d3q19.cuh",
+    for rel in ("paper_1309_1983_gb300/csrc/lbm_step_x2.cu", "paper_1309_1983_gb300/csrc/d3q19.cuh",
                 "paper_1309_1983_gb300/csrc/stream.cuh", "paper_1309_1983_gb300/csrc/internal.h"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
@@ -647,7 +647,7 @@ def run_ours(args):
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "kernel": "k_step<f32, periodic>",
+                     "kernel": "k_step_x2<f32, periodic> (two nodes per thread)",
                      "algorithmic_bytes_per_launch": bpl * cells},
         "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": 3 * 4 * cells, "d2h_bytes_per_step": 4 * 4 * cells,

@@ -139,17 +139,19 @@ int lbm_set_lid(lbm_t *h, float ux, float uy, float uz);
 /* Change tau (> 1/2). */
 int lbm_set_tau(lbm_t *h, float tau);
 
-/* Thread-block shape of the node kernels: bx threads along x (a multiple of
- * 32), by rows along y, bx * by <= 256 (x-dominant blocks, Sec. 6). The
- * default is bx = min(128, nx rounded up to 32), by = 256 / bx capped at ny. */
+/* Thread-block shape of the one-node kernels (LBM_KERNEL_NODE and BULK
+ * steps, initialisation, the slab steps of lbm_run_host): bx threads along x
+ * (a multiple of 32), by rows along y, bx * by <= 256 (x-dominant blocks,
+ * Sec. 6). The default is bx = min(128, nx rounded up to 32), by = 256 / bx
+ * capped at ny. The default two-node kernel takes lbm_set_pair_block. */
 int lbm_set_block(lbm_t *h, int bx, int by);
 
 /* Step kernel variant. LBM_KERNEL_NODE: one node per thread (every storage
  * type). LBM_KERNEL_PAIR: 16-bit storage only; two x-adjacent nodes per
  * thread with 32-bit packed loads and stores and warp shuffles for the
  * x-shifted pulls; bit-identical results (slower on GB300, like the shuffle
- * propagation the paper measured on Kepler, Sec. 4.3.2). Default: NODE for
- * FP32, LBM_KERNEL_X2 (below) for 16-bit storage. */
+ * propagation the paper measured on Kepler, Sec. 4.3.2). Default:
+ * LBM_KERNEL_X2 (below). */
 #define LBM_KERNEL_NODE 0
 #define LBM_KERNEL_PAIR 1
 /* LBM_KERNEL_BULK / BULK1: the pulled rows are staged in shared memory by
@@ -157,11 +159,11 @@ int lbm_set_block(lbm_t *h, int bx, int by);
  * 1-row tiles); bit-identical results; lbm_step_moments still uses NODE. */
 #define LBM_KERNEL_BULK 2
 #define LBM_KERNEL_BULK1 3
-/* LBM_KERNEL_X2: 16-bit storage only; two x-adjacent nodes per thread and no
- * exchange between threads: one aligned 32-bit load per pair for the 9
- * directions with e_x = 0, two 16-bit loads for the others, one packed
- * 32-bit store per direction, two-value conversions; bit-identical results.
- * Block shape: lbm_set_pair_block. */
+/* LBM_KERNEL_X2 (default, every storage type): two x-adjacent nodes per
+ * thread and no exchange between threads: one aligned two-value load per
+ * pair for the 9 directions with e_x = 0, single-value loads for the others,
+ * one two-value store per direction (16-bit: two-value conversions);
+ * bit-identical results. Block shape: lbm_set_pair_block. */
 #define LBM_KERNEL_X2 4
 int lbm_set_kernel(lbm_t *h, int variant);
 
@@ -170,8 +172,9 @@ int lbm_set_kernel(lbm_t *h, int variant);
  * node) for every node, with no divergence; LBM_WALLS_BRANCH gathers as if
  * periodic and re-reads the bounced directions only on wall nodes (fewer
  * instructions when wall nodes are rare in each warp). LBM_WALLS_AUTO
- * (default) selects for FP32 storage, for the LBM_KERNEL_X2 kernel and for
- * rows shorter than 256 nodes, else branches. The results are identical.
+ * (default) selects for FP32 storage, for the LBM_KERNEL_X2 kernel (which
+ * selects only in the warps that hold a wall node) and for rows shorter than
+ * 256 nodes, else branches. The results are identical.
  * Returns LBM_EINVAL for any other mode. */
 #define LBM_WALLS_AUTO 0
 #define LBM_WALLS_BRANCH 1
@@ -189,8 +192,8 @@ int lbm_set_wall_mode(lbm_t *h, int mode);
 int lbm_set_graph_steps(lbm_t *h, int steps);
 
 /* Block shape of the pair kernel: bxp pairs along x (a multiple of 32) by
- * `by` rows, bxp * by <= 256, used by LBM_KERNEL_PAIR and LBM_KERNEL_X2.
- * Default: 64 x 2 (1 row when ny = 1). */
+ * `by` rows, bxp * by <= 256, used by LBM_KERNEL_PAIR and LBM_KERNEL_X2
+ * (the default kernel). Default: 64 x 2 (1 row when ny = 1). */
 int lbm_set_pair_block(lbm_t *h, int bxp, int by);
 
 /* Launch-shape autotuner (no counterpart in the paper, which fixed its block

@@ -61,7 +61,8 @@ StepArgs make_args(const lbm_t *h, const void *fin, void *fout) {
   // The one-node kernel with 16-bit storage is issue-bound: there the branch
   // form's shorter common path wins once wall nodes are rare in every warp
   // (long rows). FP32 is bandwidth-bound and the divergence-free select form
-  // is never slower; the two-node 16-bit kernel is fastest with it too.
+  // is never slower; the two-node kernel selects only in the warps that hold
+  // a wall node and is fastest so.
   a.wall_select = h->wall_mode == LBM_WALLS_SELECT ||
                   (h->wall_mode == LBM_WALLS_AUTO &&
                    (h->storage == lbm::kF32 || h->nx < 256 || h->kernel == LBM_KERNEL_X2));
@@ -112,7 +113,7 @@ int ensure_scratch(lbm_t *h) {
 cudaError_t launch_one_step(const lbm_t *h, bool mom, const StepArgs &a, cudaStream_t s) {
   if (h->kernel == LBM_KERNEL_PAIR && h->storage != lbm::kF32)
     return lbm::launch_step_pair16(h->storage, mom, a, h->pbx, h->pby, s);
-  if (h->kernel == LBM_KERNEL_X2 && h->storage != lbm::kF32)
+  if (h->kernel == LBM_KERNEL_X2)
     return lbm::launch_step_x2(h->storage, mom, a, h->pbx, h->pby, s);
   if ((h->kernel == LBM_KERNEL_BULK || h->kernel == LBM_KERNEL_BULK1) && !mom)
     return lbm::launch_step_bulk(h->storage, a, h->scr.err,
@@ -316,9 +317,9 @@ int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
   if (by > ny) by = ny;
   h->bx = bx;
   h->by = by < 1 ? 1 : by;
-  // 16-bit storage: two nodes per thread (fewer instructions per node where
-  // the one-node kernel is issue-bound); FP32: one node per thread
-  h->kernel = storage == lbm::kF32 ? LBM_KERNEL_NODE : LBM_KERNEL_X2;
+  // two nodes per thread: fewer instructions per node (decisive where the
+  // one-node kernel is issue-bound, 16-bit storage; about 1% with FP32)
+  h->kernel = LBM_KERNEL_X2;
   h->wall_mode = LBM_WALLS_AUTO;
   h->pbx = 64;  // 64 pairs x 2 rows measured best for the two-node kernel
   h->pby = ny < 2 ? ny : 2;
@@ -431,8 +432,8 @@ int lbm_set_kernel(lbm_t *h, int variant) {
   if (variant != LBM_KERNEL_NODE && variant != LBM_KERNEL_PAIR && variant != LBM_KERNEL_BULK &&
       variant != LBM_KERNEL_BULK1 && variant != LBM_KERNEL_X2)
     return fail(LBM_EINVAL, "unknown kernel variant");
-  if ((variant == LBM_KERNEL_PAIR || variant == LBM_KERNEL_X2) && h->storage == lbm::kF32)
-    return fail(LBM_EINVAL, "the pair kernels need 16-bit storage");
+  if (variant == LBM_KERNEL_PAIR && h->storage == lbm::kF32)
+    return fail(LBM_EINVAL, "the shuffle pair kernel needs 16-bit storage");
   h->kernel = variant;
   h->config_version++;
   return LBM_OK;

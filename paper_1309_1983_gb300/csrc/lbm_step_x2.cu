@@ -1,24 +1,24 @@
-// lbm_step16x2.cu - the fused step (Alg. 3) for 16-bit storage with two
-// x-adjacent nodes (x0, x0 + 1), x0 even, per thread and no data exchange
-// between threads.
+// lbm_step_x2.cu - the fused step (Alg. 3) with two x-adjacent nodes
+// (x0, x0 + 1), x0 even, per thread and no data exchange between threads;
+// the default step kernel for every storage type.
 //
-// With 16-bit values the one-node kernel is bound by instruction issue, not
-// by DRAM: half the bytes per node means twice the nodes per second, and
-// every node still pays 19 load and 19 store instructions, their addresses
-// and 38 conversions. Here the two nodes of a pair share them where the
-// layout allows:
-//   * the 9 directions with e_x = 0 pull (x0 - 0, x0 + 1 - 0) from the same
-//     row: one aligned 32-bit load per pair, unpacked by one conversion per
-//     half;
+// The two nodes of a pair share what the SoA layout lets them share:
+//   * the 9 directions with e_x = 0 pull (x0, x0 + 1) from the same row: one
+//     aligned 8-byte (FP32) or 4-byte (16-bit) load per pair;
 //   * the 10 directions with e_x != 0 pull from x0 - e_x and x0 + 1 - e_x,
-//     an odd offset: two 16-bit loads (the misaligned-read variant of
+//     an odd offset: two single-value loads (the misaligned-read variant of
 //     Sec. 4.3.2, as in the one-node kernel);
-//   * all 19 results are stored as one aligned 32-bit word per pair, packed
-//     by one two-value conversion.
+//   * all 19 results leave as one aligned two-value store per pair (for
+//     16-bit storage after one two-value conversion).
+// With 16-bit values the one-node kernel is bound by instruction issue (half
+// the bytes per node means twice the nodes per second, and every node still
+// pays 19 loads, 19 stores, their addresses and 38 conversions): sharing
+// them takes 40 instructions per node off. With FP32 the kernel is
+// DRAM-bound and the pairs add about 1% of throughput.
 // The arithmetic per node is that of the one-node kernel (same collision,
 // same round-to-nearest-even conversions), so both produce identical bits.
 // On an odd-length row the last pair's second node lies in the row padding
-// (the pitch is a multiple of 16 values): it is loaded and stored but never
+// (the pitch is a multiple of 32 bytes): it is loaded and stored but never
 // used.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -29,11 +29,28 @@
 
 namespace lbm {
 
+// Loads and stores of an aligned pair of values, as two floats.
 template <int S>
 struct Pack16;
 
 template <>
+struct Pack16<0> {
+  static __device__ __forceinline__ float2 load(const float *p) {
+    return __ldg(reinterpret_cast<const float2 *>(p));
+  }
+  static __device__ __forceinline__ void store(float *p, float lo, float hi) {
+    __stcs(reinterpret_cast<float2 *>(p), make_float2(lo, hi));
+  }
+};
+
+template <>
 struct Pack16<1> {
+  static __device__ __forceinline__ float2 load(const __half *p) {
+    return unpack(__ldg(reinterpret_cast<const unsigned int *>(p)));
+  }
+  static __device__ __forceinline__ void store(__half *p, float lo, float hi) {
+    __stcs(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
+  }
   static __device__ __forceinline__ float2 unpack(uint32_t v) {
     return __half22float2(*reinterpret_cast<const __half2 *>(&v));
   }
@@ -45,6 +62,12 @@ struct Pack16<1> {
 
 template <>
 struct Pack16<2> {
+  static __device__ __forceinline__ float2 load(const __nv_bfloat16 *p) {
+    return unpack(__ldg(reinterpret_cast<const unsigned int *>(p)));
+  }
+  static __device__ __forceinline__ void store(__nv_bfloat16 *p, float lo, float hi) {
+    __stcs(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
+  }
   static __device__ __forceinline__ float2 unpack(uint32_t v) {
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v));
   }
@@ -56,7 +79,7 @@ struct Pack16<2> {
 
 // Pulled values of both nodes for direction i (bounce-back by address
 // selection when SEL; the e_x = 0 pulls of the pair share y, z, hence their
-// wall decisions, so they stay one 32-bit load).
+// wall decisions, so they stay one paired load).
 template <int S, bool SEL, int i>
 __device__ __forceinline__ void pull_pair(const typename Store<S>::T *__restrict__ fin,
                                           uint32_t plane, const NodeIdx &n0, const NodeIdx &n1,
@@ -67,7 +90,7 @@ __device__ __forceinline__ void pull_pair(const typename Store<S>::T *__restrict
     if constexpr (SEL) {
       if (bounces<i>(n0)) idx = (size_t)kOpp_v<i> * plane + n0.c;
     }
-    const float2 p = Pack16<S>::unpack(__ldg(reinterpret_cast<const unsigned int *>(fin + idx)));
+    const float2 p = Pack16<S>::load(fin + idx);
     v0 = p.x;
     v1 = p.y;
   } else {
@@ -87,7 +110,8 @@ __device__ __forceinline__ void pull_pair(const typename Store<S>::T *__restrict
 }
 
 // Launch bounds: by default only the block size is fixed (64 registers for
-// the periodic kernel, 74-80 with walls); LBM_X2_MIN_BLOCKS asks for that
+// the periodic 16-bit kernel, 74 for FP32, up to 80 with walls);
+// LBM_X2_MIN_BLOCKS asks for that
 // many resident 256-thread blocks per SM instead (tuning experiments).
 #ifdef LBM_X2_MIN_BLOCKS
 #define LBM_X2_BOUNDS __launch_bounds__(256, LBM_X2_MIN_BLOCKS)
@@ -156,8 +180,7 @@ __global__ void LBM_X2_BOUNDS k_step_x2(const StepArgs a) {
   collide<FORCE>(d1, a.omega, a.kf, F1x, F1y, F1z, r1, u1x, u1y, u1z);
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    __stcs(reinterpret_cast<unsigned int *>(fout + (size_t)i * a.plane + n0.c),
-           Pack16<S>::pack(d0[i], d1[i]));
+    Pack16<S>::store(fout + (size_t)i * a.plane + n0.c, d0[i], d1[i]);
   });
   if constexpr (MOM) {
     a.rho[dc] = r0;
@@ -202,6 +225,7 @@ cudaError_t launch_step_x2(int storage, bool moments, const StepArgs &a, int bxp
   const int pairs = (a.nx + 1) / 2;
   const dim3 g((pairs + bxp - 1) / bxp, (a.ny + by - 1) / by, a.zn), b(bxp, by, 1);
   switch (storage) {
+    case kF32: x2_dispatch<0>(moments, a, g, b, s); break;
     case kF16: x2_dispatch<1>(moments, a, g, b, s); break;
     case kBF16: x2_dispatch<2>(moments, a, g, b, s); break;
     default: return cudaErrorInvalidValue;

@@ -184,9 +184,10 @@ def test_kernel_variants_need_matching_storage(lib):
     h32 = capi.create(8, 8, 8, 0.8, capi.LBM_STORE_F32)
     h16 = capi.create(8, 8, 8, 0.8, capi.LBM_STORE_F16)
     try:
+        assert lib.lbm_set_kernel(h32, capi.LBM_KERNEL_PAIR) == capi.LBM_EINVAL
         for v in (capi.LBM_KERNEL_PAIR, capi.LBM_KERNEL_X2):
-            assert lib.lbm_set_kernel(h32, v) == capi.LBM_EINVAL
             assert lib.lbm_set_kernel(h16, v) == 0
+        assert lib.lbm_set_kernel(h32, capi.LBM_KERNEL_X2) == 0
         assert lib.lbm_set_kernel(h16, 5) == capi.LBM_EINVAL
         assert lib.lbm_set_kernel(h32, capi.LBM_KERNEL_NODE) == 0
     finally:

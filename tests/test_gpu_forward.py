@@ -263,12 +263,19 @@ def test_nonfinite_density_is_reported():
 
 @pytest.mark.parametrize("block", [(32, 1), (32, 8), (64, 4), (128, 2), (256, 1)])
 def test_block_shapes_agree(block):
-    """Every supported block shape computes the same bits."""
+    """Every supported block shape of the one-node kernel computes the same
+    bits, and so does every pair-block shape of the two-node kernel."""
     L = _lat(70, 13, 5, 0.7, (1, 1, 1), (0.05, 0, 0))
+    L.set_kernel("node")
     L.init_equilibrium()
     L.step(4)
     ref = L.get_f()
     L.set_block(*block)
+    L.init_equilibrium()
+    L.step(4)
+    np.testing.assert_array_equal(L.get_f(), ref)
+    L.set_kernel("x2")
+    L.set_pair_block(*block)
     L.init_equilibrium()
     L.step(4)
     np.testing.assert_array_equal(L.get_f(), ref)
@@ -387,3 +394,32 @@ def test_graph_replay_matches_plain_launches(storage):
         np.testing.assert_array_equal(f, runs[0][0])
         np.testing.assert_array_equal(r, runs[0][1])
         np.testing.assert_array_equal(v, runs[0][2])
+
+
+@pytest.mark.parametrize("mode", ["select", "branch"])
+@pytest.mark.parametrize("geom", sorted(GEOMS))
+@pytest.mark.parametrize("shape", [(37, 11, 9), (64, 5, 3), (1, 7, 6), (3, 4, 5), (130, 3, 2)],
+                         ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("force", [False, True])
+def test_two_node_kernel_is_bit_identical_fp32(geom, shape, force, mode):
+    """The default two-node kernel computes the one-node kernel's bits in
+    FP32 too: odd and 1-wide rows, every geometry, both wall forms, a body
+    force and the fused moment output."""
+    nx, ny, nz = shape
+    g = GEOMS[geom]
+    OL = _olat(nx, ny, nz, 0.6)
+    f0 = _random_state(OL, 8)
+    F = torch.from_numpy(W.noise((3,) + OL.shape, 9, 1e-3)).float()
+    outs = []
+    for kern in ("node", "x2"):
+        L = _lat(nx, ny, nz, 0.6, g["walls"], g["lid"], force=force)
+        L.set_kernel(kern)
+        L.set_wall_mode(mode)
+        if force:
+            L.force.copy_(F)
+        L.set_f(f0)
+        L.step(3)
+        rho, u = L.step_moments(2)
+        outs.append((L.get_f(), rho.cpu(), u.cpu()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    assert torch.equal(outs[0][1], outs[1][1]) and torch.equal(outs[0][2], outs[1][2])
