@@ -114,11 +114,25 @@ __device__ __forceinline__ void shifted_moments(const float (&d)[Q], float &dr,
 
 // ---- BGK collision with optional Guo force, in place on shifted values -----
 // In: d_i = g_i - w_i (post-streaming). Out: d*_i = f*_i - w_i with
-//   f*_i = g_i + omega (f^eq_i - g_i) + kf S_i,  kf = 1 - omega/2,
-//   f^eq_i - w_i = w_i [dr + rho (3 eu + 4.5 eu^2 - 1.5 u^2)]      (Eq. 5)
-//   S_i = w_i [3 (e_i - u) + 9 eu e_i] . F                            (Guo)
+//   f*_i = (1 - omega) g_i + omega f^eq_i + kf S_i,  kf = 1 - omega/2,
+// and f^eq_i - w_i (Eq. 5) split into its parts even and odd in e_i, written
+// with the momentum j = rho u = sum e_i g_i + F/2:
+//   even_i = w_i [dr - 1.5 |j|^2 / rho + 4.5 (e_i . j)^2 / rho]
+//   odd_i  = 3 w_i (e_i . j)                  (no division by rho enters it)
+//   S_i    = w_i [3 (e_i - u) + 9 (e_i . u) e_i] . F                (Guo)
 // Each opposite pair (i, i+1) shares its even part and negates its odd part.
-// Returns rho and the velocity u = (j + F/2)/rho that the collision used.
+//
+// Momentum is the quantity that rounding must not bias. The odd parts return
+// (2 c_A + 8 c_B) j with c_A = 3 w_A omega = omega/6 and c_B = omega/12, and
+// the relaxed part (1 - omega) j. With FP32-rounded coefficients the sum is
+// (1 + delta) j, delta ~ 1e-7, on every node and every step: over 1000 steps
+// of a freely decaying flow that drift reaches ~1e-4 of the velocity. The
+// host therefore sets omega within 2^-22 of 1/tau such that omega * (1/12)
+// is exactly omega/12 in FP32 and 12 times it is exactly omega (see
+// relaxation_rate); then c_A = 2 c_B, 2 c_A + 8 c_B = omega and 1 - omega
+// are all exact, and the step conserves momentum up to unbiased per-node
+// rounding.
+// Returns rho and the velocity u = j / rho that the collision used.
 template <bool FORCE>
 __device__ __forceinline__ void collide(float (&d)[Q], float omega, float kf,
                                         float Fx, float Fy, float Fz,
@@ -136,23 +150,26 @@ __device__ __forceinline__ void collide(float (&d)[Q], float omega, float kf,
   ux = jx * rinv;
   uy = jy * rinv;
   uz = jz * rinv;
-  const float usq15 = 1.5f * fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-  float uF = 0.0f;
-  if constexpr (FORCE) uF = fmaf(ux, Fx, fmaf(uy, Fy, uz * Fz));
-  // f*_i = (1 - omega) g_i + omega f^eq_i, with omega folded into the
-  // weights. The velocity is pre-scaled by sqrt(9/2) so that one FMA gives
-  // 4.5 (e.u)^2 - 1.5 u^2; the odd part 3 w rho (e.u) then takes one multiply
-  // by a per-weight-class factor.
-  constexpr float kS = 2.12132034355964257f;  // sqrt(9/2)
-  const float keep = 1.0f - omega;
-  const float vx = kS * ux, vy = kS * uy, vz = kS * uz;
+  const float keep = 1.0f - omega;              // exact
+  const float cB = omega * (1.0f / 12.0f);      // exactly omega/12
+  const float cA = 2.0f * cB;                   // exactly omega/6
+  const float jsq = fmaf(jx, jx, fmaf(jy, jy, jz * jz));
+  const float base = fmaf(-1.5f * jsq, rinv, dr);  // dr - 1.5 rho |u|^2
+  const float k45 = 4.5f * rinv;
+  // omega folded into the weights of the even part
   const float owA = omega * weight(1), owB = omega * weight(7);
-  const float roA = ((3.0f / kS) * rho) * owA, roB = ((3.0f / kS) * rho) * owB;
+  const float bA = owA * base, bB = owB * base;
+  const float kA = owA * k45, kB = owB * k45;
+  float uF = 0.0f, k9 = 0.0f;
+  if constexpr (FORCE) {
+    uF = fmaf(ux, Fx, fmaf(uy, Fy, uz * Fz));
+    k9 = 9.0f * rinv;
+  }
 
   // rest direction
   {
     constexpr float w = weight(0);
-    float v = fmaf(keep, d[0], (omega * w) * fmaf(-rho, usq15, dr));
+    float v = fmaf(keep, d[0], (omega * w) * base);
     if constexpr (FORCE) v = fmaf(kf, w * (-3.0f * uF), v);
     d[0] = v;
   }
@@ -161,15 +178,15 @@ __device__ __forceinline__ void collide(float (&d)[Q], float omega, float kf,
     constexpr int j = i + 1;                        // its opposite
     constexpr float w = weight(i);
     constexpr float cx = (float)kEx[i], cy = (float)kEy[i], cz = (float)kEz[i];
-    const float ow = i < 7 ? owA : owB, ro = i < 7 ? roA : roB;
-    const float es = cx * vx + cy * vy + cz * vz;  // sqrt(9/2) e.u; folds to adds/subs
-    const float even = ow * fmaf(rho, fmaf(es, es, -usq15), dr);
-    const float odd = ro * es;
+    const float b = i < 7 ? bA : bB, k = i < 7 ? kA : kB, c = i < 7 ? cA : cB;
+    const float es = cx * jx + cy * jy + cz * jz;  // e.j; folds to adds/subs
+    const float even = fmaf(es * es, k, b);
+    const float odd = c * es;
     float vi = fmaf(keep, d[i], even + odd);
     float vj = fmaf(keep, d[j], even - odd);
     if constexpr (FORCE) {
       const float eF = cx * Fx + cy * Fy + cz * Fz;
-      const float sEven = w * fmaf((9.0f / kS) * es, eF, -3.0f * uF);
+      const float sEven = w * fmaf(k9 * es, eF, -3.0f * uF);  // 9 (e.u)(e.F) - 3 u.F
       const float sOdd = (3.0f * w) * eF;
       vi = fmaf(kf, sEven + sOdd, vi);
       vj = fmaf(kf, sEven - sOdd, vj);

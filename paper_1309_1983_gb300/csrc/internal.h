@@ -114,6 +114,12 @@ struct BatchArgs {
   unsigned long long timeout_ns;
 };
 
+// Relaxation rate omega passed to every kernel for a relaxation time tau:
+// the FP32 value within 2^-22 (relative) of 1/tau for which omega * (1/12)
+// is exactly omega/12 in FP32 and 12 times that is exactly omega (the
+// momentum-exact coefficients of collide() in d3q19.cuh).
+float relaxation_rate(float tau);
+
 // Record a failure for lbm_last_error() (thread-local) and return code.
 int set_error(int code, const char *what);
 int set_cuda_error(cudaError_t e, const char *where);

@@ -175,7 +175,7 @@ int lbm_batch_create(int ndom, const int *dims, const float *tau, const float *l
     D.walls = flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z);
     D.m_nx = magic42((uint32_t)nx);
     D.m_nxy = magic42((uint32_t)(nx * ny));
-    D.omega = 1.0f / t;
+    D.omega = lbm::relaxation_rate(t);
     D.kf = 1.0f - 0.5f * D.omega;
     const double ux = (lid_ux && (flags & LBM_LID)) ? (double)lid_ux[k] : 0.0;
     for (int i = 0; i < lbm::Q; ++i)

@@ -16,6 +16,36 @@
 
 using lbm::StepArgs;
 
+namespace lbm {
+
+float relaxation_rate(float tau) {
+  // c = omega/12 on a grid of 22 significant bits, so that 12 c needs at
+  // most 24 bits and is an exact FP32 value, and of multiples of 2^-26, so
+  // that omega = 12 c is a multiple of 2^-24 and 1 - omega is exact too
+  // (this coarsens omega below 1/2, i.e. tau > 2, to 2^-24 absolute). Among
+  // the grid points nearest to 1/(12 tau), take one that the kernels'
+  // product omega * (1/12) reproduces exactly.
+  const double c0 = 1.0 / (12.0 * (double)tau);
+  int e = 0;
+  frexp(c0, &e);  // c0 in [2^(e-1), 2^e)
+  const double q = fmax(ldexp(1.0, e - 22), ldexp(1.0, -26));
+  const double cr = nearbyint(c0 / q) * q;
+  for (int k = 0; k < 64; ++k) {
+    const double cand = cr + (k % 2 ? -1.0 : 1.0) * (double)((k + 1) / 2) * q;
+    if (!(cand > 0.0)) continue;
+    volatile float c = (float)cand;
+    volatile float om = 12.0f * c;
+    volatile float back = om * (1.0f / 12.0f);
+    volatile float keep = 1.0f - om;
+    if ((double)c == cand && (double)om == 12.0 * cand && back == c &&
+        (double)keep == 1.0 - 12.0 * cand)
+      return om;
+  }
+  return (float)(1.0 / (double)tau);  // tau beyond ~4e6: no such value
+}
+
+}  // namespace lbm
+
 namespace {
 
 thread_local char g_last_error[256] = "";
@@ -53,7 +83,7 @@ StepArgs make_args(const lbm_t *h, const void *fin, void *fout) {
   a.pitch = h->pitch;
   a.plane = (uint32_t)h->plane;
   a.cells = (uint32_t)((size_t)h->nx * h->ny * h->nz);
-  a.omega = 1.0f / h->tau;
+  a.omega = lbm::relaxation_rate(h->tau);
   a.kf = 1.0f - 0.5f * a.omega;
   a.walls = h->flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z);
   a.z0 = 0;
