@@ -56,8 +56,9 @@ def test_one_step_within_storage_rounding(storage, shape):
 def test_sixteen_bit_error_vs_oracle_64_after_5000_steps(tmp_path):
     """Cavity 64^3 (tau = 0.55, lid 0.05) after 5000 steps with FP32, FP16
     and BF16 storage against the FP64 oracle: the error of each is recorded
-    (max and relative L2 of rho and u); FP32 must meet 1e-4 and FP16 1e-2 of
-    the velocity field maximum, BF16 must stay bounded (no blow-up)."""
+    (max and relative L2 of rho and u); FP32 must meet the stated 1e-5 of
+    the velocity field maximum (measured 6.4e-7), FP16 1e-2, and BF16 must
+    stay bounded (no blow-up)."""
     n, tau, steps = 64, 0.55, 5000
     OL = O.Lattice(n, n, n, tau, walls=(True, True, True), lid=True, lid_u=(0.05, 0, 0))
     rr, ur = O.moments(OL, O.run(OL, O.init_equilibrium(OL), steps))
@@ -78,7 +79,7 @@ def test_sixteen_bit_error_vs_oracle_64_after_5000_steps(tmp_path):
         with open(os.path.join(out, "storage16_error_64cube_5000.json"), "w") as fh:
             json.dump(report, fh, indent=1)
     print(json.dumps(report))
-    assert report["f32"]["u_max_rel"] < 1e-4, report
+    assert report["f32"]["u_max_rel"] < 1e-5, report
     assert report["f16"]["u_max_rel"] < 1e-2, report
     assert report["bf16"]["u_max_rel"] < 0.5 and np.isfinite(report["bf16"]["rho_max"]), report
 
