@@ -103,7 +103,11 @@ const char *lbm_last_error(void);
  * and LBM_* flags. Host-only: no CUDA call is made. Requires every size >= 1,
  * tau > 1/2, at most one LBM_STORE_* value, LBM_LID only with LBM_WALL_Z,
  * LBM_ADJOINT only with FP32 storage, and nz * ny * pitch < 2^31. On
- * success *out owns the handle. */
+ * success *out owns the handle. The kernels relax with omega = 1/tau rounded
+ * to the nearest FP32 value whose twelfth is exact (within 2^-22 of 1/tau for
+ * tau <= 2, 2^-24 absolute above): the collision's momentum coefficients then
+ * sum to exactly omega, so FP32 rounding does not bias the momentum step
+ * after step. The same holds for lbm_set_tau and lbm_batch_create. */
 int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
                lbm_t **out);
 
@@ -279,12 +283,15 @@ int lbm_moments(lbm_t *h, float *rho, float *u, double *mass);
  * cudaMalloc, cudaFree or allocating library routine: its reduction scratch is
  * a fixed 9.75 KiB static device array per GPU, created when the library's
  * device code is loaded on that GPU and kept until the process exits. The
- * first call on each device looks up that array's device address
+ * first call in each CUDA context (per device, and again in a new context
+ * after cudaDeviceReset) looks up that array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream capture.
  * All calls on a device share the array: calls that overlap on the GPU
- * (other streams or threads at the same time) race on it. Limit: nz * ny *
- * pitch < 2^31 nodes (as for lbm_create); larger sizes return LBM_ERANGE
- * without launching anything. */
+ * (other streams or threads at the same time) race on it. Unlike
+ * lbm_moments, this call does no non-finite check and never returns
+ * LBM_ENONFINITE: a non-finite density shows only as a non-finite rho and
+ * *mass. Limit: nz * ny * pitch < 2^31 nodes (as for lbm_create); larger
+ * sizes return LBM_ERANGE without launching anything. */
 int lbm_moments_noalloc(const void *f, int nx, int ny, int nz, uint32_t flags,
                         const float *force, float *rho, float *u, double *mass,
                         void *stream);

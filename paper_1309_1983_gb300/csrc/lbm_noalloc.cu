@@ -10,12 +10,19 @@
 // reduction scratch in the file-scope array below instead.
 //
 // The array exists once per GPU (it is created when the library's device code
-// is loaded on that GPU) and stays until the process exits. Every call on a device
-// shares it, so calls whose work overlaps on the GPU (different streams,
-// or host threads racing) race on it; order them on one stream. The array
-// keeps the last call's contents: the per-block partial sums are fully
-// rewritten by each call before they are read, and the error word is cleared
-// at the start of each call.
+// is loaded on that GPU) and stays until the process exits. Every call on a
+// device shares it, so calls whose work overlaps on the GPU (different
+// streams, or host threads racing) race on it; order them on one stream. The
+// array keeps the last call's contents: the per-block partial sums are fully
+// rewritten by each call before they are read. The moment kernel also sets a
+// non-finite flag in the word after them; nothing reads that word here (the
+// call does no non-finite check: a non-finite density makes the FP64 mass
+// non-finite), so it is never cleared.
+//
+// In host code the array's name is only a stand-in for the device symbol: its
+// device address is looked up with cudaGetSymbolAddress, once per CUDA
+// context (a context created after cudaDeviceReset, or another context made
+// current, gets its own lookup), and only that address is passed to kernels.
 #include <string.h>
 
 #include <mutex>
@@ -25,26 +32,69 @@
 
 namespace {
 
-// kReduceBlocks FP64 partial sums, then one int error word (in the next
+// kReduceBlocks FP64 partial sums, then one int flag word (in the next
 // double slot), padded to a multiple of 256 bytes: 9.75 KiB per GPU.
 constexpr int kNoallocSlots = lbm::kReduceBlocks + 32;
+static_assert(kNoallocSlots >= lbm::kReduceBlocks + 1,
+              "partials (at most kReduceBlocks: moments_blocks clamps to it) + flag word");
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocSlots];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-double *g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchAddr {
+  unsigned long long ctx_id;  // cuCtxGetId of the context the address belongs to
+  double *addr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the array on the current device; the host-side symbol is
-// only a stand-in and must never be handed to a kernel.
+// Context queries through the runtime's driver entry points (no link-time
+// dependency on libcuda).
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+bool g_entry_points_loaded = false;
+
+// Unique id of the current context, 0 if there is none or it cannot be
+// queried. Called with g_setup_mutex held.
+unsigned long long current_context_id() {
+  if (!g_entry_points_loaded) {
+    g_entry_points_loaded = true;
+    void *fa = nullptr, *fb = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fa, 12000, cudaEnableDefault,
+                                         &qa) == cudaSuccess &&
+        qa == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &fb, 12000, cudaEnableDefault, &qb) ==
+            cudaSuccess &&
+        qb == cudaDriverEntryPointSuccess) {
+      g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fa);
+      g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(fb);
+    }
+    cudaGetLastError();
+  }
+  if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != 0 || !ctx) return 0;
+  if (g_ctx_get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the array in the current context of device `dev`; the
+// host-side symbol is only a stand-in and must never be handed to a kernel.
 int scratch_address(int dev, double **out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  ScratchAddr &slot = g_scratch_addr[dev];
+  const unsigned long long id = current_context_id();
+  if (!slot.addr || id == 0 || slot.ctx_id != id) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return lbm::set_cuda_error(e, "cudaGetSymbolAddress");
-    g_scratch_addr[dev] = static_cast<double *>(p);
+    slot.addr = static_cast<double *>(p);
+    slot.ctx_id = current_context_id();  // the lookup makes the context current
   }
-  *out = g_scratch_addr[dev];
+  *out = slot.addr;
   return LBM_OK;
 }
 
@@ -68,9 +118,7 @@ extern "C" int lbm_moments_noalloc(const void *f, int nx, int ny, int nz, uint32
     return lbm::set_error(LBM_ERANGE,
                           "lbm_moments_noalloc: nz * ny * pitch must be < 2^31 nodes");
   const uint32_t cells = (uint32_t)((long long)nx * ny * nz);
-  const int nparts = lbm::moments_blocks(cells);
-  if (nparts > lbm::kReduceBlocks)
-    return lbm::set_error(LBM_ERANGE, "lbm_moments_noalloc: reduction exceeds static scratch");
+  const int nparts = lbm::moments_blocks(cells);  // <= kReduceBlocks by construction
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return lbm::set_cuda_error(e, "cudaGetDevice");
@@ -97,10 +145,6 @@ extern "C" int lbm_moments_noalloc(const void *f, int nx, int ny, int nz, uint32
   scr.sum = nullptr;
   scr.err = reinterpret_cast<int *>(scratch + lbm::kReduceBlocks);
   scr.nblocks = lbm::kReduceBlocks;
-  if (mass) {
-    e = cudaMemsetAsync(scr.err, 0, sizeof(int), s);
-    if (e != cudaSuccess) return lbm::set_cuda_error(e, "error word clear");
-  }
   e = lbm::launch_moments(storage, a, f, rho, u, mass ? &scr : nullptr, s);
   if (e != cudaSuccess) return lbm::set_cuda_error(e, "moments kernel launch");
   if (mass) {

@@ -3,11 +3,15 @@ callers that cannot allocate device memory (memory owned by another
 allocator, or loops where cudaMalloc/cudaFree would synchronise the device).
 
 It is checked through the C ABI against lbm_moments, the handle-based entry
-point, on two calls in a row: a larger FP32 lattice with a body force, then a
-smaller FP16 lattice, so the second call runs on scratch that still holds the
-first call's partial sums. Tolerances are those of the moment tests: 1e-6 on
-rho and u, 1e-9 relative on the FP64 mass. This file is named so that pytest
-collects it last.
+point (itself checked against the FP64 oracle in test_gpu_forward.py):
+* two calls in a row, a larger FP32 lattice with a body force and then a
+  smaller FP16 lattice, so the second call runs on scratch that still holds
+  the first call's partial sums;
+* every storage type (FP32, FP16, BF16);
+* the optional outputs left out one at a time (no mass: no reduction and no
+  scratch use; no u; no rho).
+Tolerances are those of the moment tests: 1e-6 on rho and u, 1e-9 relative
+on the FP64 mass. This file is named so that pytest collects it last.
 """
 
 import ctypes
@@ -40,7 +44,7 @@ def _random_state(nx, ny, nz, tau, seed):
     return f * (1.0 + W.noise(f.shape, seed + 2, 0.1))
 
 
-def _compare(L, force):
+def _compare(L, force, want_rho=True, want_u=True, want_mass=True):
     from paper_1309_1983_gb300 import capi
     lib = capi.load()
     rho_ref, u_ref, mass_ref = L.moments(mass=True)
@@ -49,13 +53,24 @@ def _compare(L, force):
     u = torch.full_like(u_ref, float("nan"))
     mass = torch.full((), float("nan"), dtype=torch.float64, device="cuda")
     rc = lib.lbm_moments_noalloc(_p(cur), L.nx, L.ny, L.nz, L.flags,
-                                 None if force is None else _p(force), _p(rho), _p(u), _p(mass),
+                                 None if force is None else _p(force),
+                                 _p(rho) if want_rho else None, _p(u) if want_u else None,
+                                 _p(mass) if want_mass else None,
                                  ctypes.c_void_p(L.stream.cuda_stream))
     assert rc == capi.LBM_OK, capi.last_error()
     L.stream.synchronize()
-    torch.testing.assert_close(rho, rho_ref, rtol=0, atol=1e-6)
-    torch.testing.assert_close(u, u_ref, rtol=0, atol=1e-6)
-    assert abs(mass.item() - mass_ref) <= 1e-9 * abs(mass_ref)
+    if want_rho:
+        torch.testing.assert_close(rho, rho_ref, rtol=0, atol=1e-6)
+    else:
+        assert torch.isnan(rho).all()  # left untouched
+    if want_u:
+        torch.testing.assert_close(u, u_ref, rtol=0, atol=1e-6)
+    else:
+        assert torch.isnan(u).all()
+    if want_mass:
+        assert abs(mass.item() - mass_ref) <= 1e-9 * abs(mass_ref)
+    else:
+        assert np.isnan(mass.item())
 
 
 def test_noalloc_moments_match_handle_moments_twice():
@@ -71,6 +86,19 @@ def test_noalloc_moments_match_handle_moments_twice():
     L2.set_f(_random_state(17, 9, 5, 0.6, 11))
     L2.step(2)
     _compare(L2, None)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("outputs", ["all", "no_mass", "no_u", "no_rho"])
+def test_noalloc_storage_types_and_optional_outputs(storage, outputs):
+    from paper_1309_1983_gb300.lattice import Lattice
+    nx, ny, nz = 37, 12, 7
+    L = Lattice(nx, ny, nz, 0.65, walls=(True, False, True), lid=(0.04, 0.0, 0.0),
+                storage=storage)
+    L.set_f(_random_state(nx, ny, nz, 0.65, 21))
+    L.step(2)
+    _compare(L, None, want_rho=outputs != "no_rho", want_u=outputs != "no_u",
+             want_mass=outputs != "no_mass")
 
 
 def test_noalloc_rejects_sizes_beyond_the_maximum():
