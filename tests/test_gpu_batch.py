@@ -181,3 +181,82 @@ def test_batched_adjoint_forms_agree():
         res.append([t.cpu().numpy() for t in P.loss_and_grad(u0, torch.zeros_like(u0), ut)])
     for a, b in zip(*res):
         np.testing.assert_array_equal(a, b)
+
+
+def _axis_block(n, c):
+    """Indices of the oracle block along one walled axis, and the node's
+    position in it: the node and its neighbours, cut at the walls."""
+    lo, hi = max(c - 1, 0), min(c + 1, n - 1)
+    return list(range(lo, hi + 1)), c - lo
+
+
+def _large_domain_samples(nx, ny, nz, threads, rng, count=48):
+    """Corners, face centres, and nodes on both sides of tile boundaries
+    (tiles are `threads` consecutive nodes in dense order), including tiles
+    that cross from one z plane into the next; then random nodes."""
+    def node(dc):
+        return (dc % nx, (dc // nx) % ny, dc // (nx * ny))
+    pts = {(x, y, z) for x in (0, nx - 1) for y in (0, ny - 1) for z in (0, nz - 1)}
+    pts |= {(nx // 2, ny // 2, 0), (nx // 2, ny // 2, nz - 1), (0, ny // 2, nz // 2),
+            (nx - 1, ny // 2, nz // 2), (nx // 2, 0, nz // 2), (nx // 2, ny - 1, nz // 2)}
+    plane, cells = nx * ny, nx * ny * nz
+    crossing = [k for k in range(1, nz) if (k * plane) % threads != 0]
+    for k in crossing[:4] + crossing[-2:]:  # z-plane seam inside a tile
+        pts |= {node(k * plane - 1), node(k * plane)}
+    for t in (1, 2, cells // threads // 2, cells // threads - 1):  # tile seams
+        if 0 < t * threads < cells:
+            pts |= {node(t * threads - 1), node(t * threads)}
+    while len(pts) < count:
+        pts.add((int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz))))
+    return sorted(pts)
+
+
+@pytest.mark.parametrize("tiling", [None, (128, 0)])
+def test_sixty_four_cavities_large_domains_sampled_parity(tiling):
+    """One persistent step of the seeded 64-cavity workload from random
+    non-equilibrium states in its five largest domains; on >= 48 sampled
+    nodes per domain (corners, faces, both sides of tile seams and of tiles
+    that cross a z plane, random nodes) f^{n+1} matches one oracle step on
+    the node's neighbourhood block within 1e-6. These domains (up to 96^3
+    nodes) reach tile indices and node decodes the small-domain tests do
+    not."""
+    from paper_1309_1983_gb300.batch import Batch
+    G = W.batch_geometry(64, seed=3)
+    B = Batch(G.dims, G.tau, G.lid_u)
+    if tiling:
+        B.set_tiling(*tiling)
+    threads = B.info()["threads"]
+    B.init_rest()
+    cells = G.dims.prod(axis=1)
+    large = [int(d) for d in np.argsort(cells)[-5:]]
+    rng = np.random.default_rng(5)
+    blocks = {}
+    for d in large:
+        OL = _olat(G.dims[d], G.tau[d], G.lid_u[d])
+        f0 = _random_f(OL, 100 + d)
+        B.set_f(d, f0)
+        nx, ny, nz = OL.nx, OL.ny, OL.nz
+        samples = _large_domain_samples(nx, ny, nz, threads, rng)
+        assert len(samples) >= 48
+        blocks[d] = []
+        for (x, y, z) in samples:
+            xi, cx = _axis_block(nx, x)
+            yi, cy = _axis_block(ny, y)
+            zi, cz = _axis_block(nz, z)
+            sub = np.ascontiguousarray(f0[:, zi][:, :, yi][:, :, :, xi])
+            # the block is walled (or lid-covered) only where it touches the
+            # lattice's own faces; a cut inside the lattice would be wrong for
+            # the node's neighbours but not for the node itself, whose pulls
+            # all come from inside the block
+            OB = O.Lattice(len(xi), len(yi), len(zi), OL.tau, walls=(True, True, True),
+                           lid=zi[-1] == nz - 1, lid_u=OL.lid_u)
+            blocks[d].append(((x, y, z), sub, OB, (cx, cy, cz)))
+    B.step(1)
+    assert B.info()["graph"]
+    for d in large:
+        f1 = B.get_f(d)
+        worst = 0.0
+        for (x, y, z), sub, OB, (cx, cy, cz) in blocks[d]:
+            ref = O.run(OB, sub, 1)[:, cz, cy, cx]
+            worst = max(worst, float(np.abs(f1[:, z, y, x] - ref).max()))
+        assert worst <= 1e-6, (d, tuple(G.dims[d]), worst)
