@@ -27,6 +27,23 @@
  * else zero. (The paper itself used on-site velocity conditions for the
  * cavity, Sec. 5; the halfway rule is the one this library implements.)
  *
+ * On-site velocity boundary (the scheme the paper used for its cavity,
+ * Sec. 5, citing Hecht & Harting's D3Q19 on-site conditions), selected by
+ * the lattice's `onsite` field: the walls of a walled axis then lie ON its
+ * first and last node planes. Those nodes stream and collide like any other;
+ * after streaming, the populations they would pull from outside the lattice
+ * (unknown) are rebuilt so that the node has the prescribed velocity u_w
+ * (lid velocity on the top plane z = nz-1, zero elsewhere). The rule is the
+ * Zou-He non-equilibrium bounce-back with Hecht & Harting's transverse
+ * momentum correction, stated as constraints and solved here directly:
+ *   unknown i, opposite known:  g_i = g_ibar + 6 w_i (e_i . j) - e_i . N
+ *   "buried" pairs (i and ibar both unknown): equal values b
+ * with j = rho u_w - F/2 (so that (sum e g + F/2)/rho = u_w), N the vector
+ * that makes sum e_i g_i = j exactly (a 3x3 linear system), and mass fixing
+ * rho on a face (rho = sum g) or, where the node lies on two or three walled
+ * faces (edges, corners), fixing b, rho being then taken from the stored
+ * state of the node one step inward along the diagonal.
+ *
  * The discrete adjoint (gradient of L = 1/2 sum |u(T) - u_target|^2 with
  * respect to the initial velocity and the per-cell force) is computed with
  * an explicit dense 19x19 collision Jacobian per cell and a scatter-form
@@ -72,6 +89,7 @@ typedef struct {
   int lid;                    /* 1: the plane z = nz moves with lid_u */
   double tau;
   double lid_u[3];
+  int onsite;                 /* 1: on-site velocity walls (see above) */
 } oracle_lattice;
 
 /* ---- introspection (used by the tests to pin the tables to the paper) ---- */
@@ -108,6 +126,10 @@ static int check_lattice(const oracle_lattice *L) {
   if (!L || L->nx < 1 || L->ny < 1 || L->nz < 1) return -1;
   if (!(L->tau > 0.5)) return -1;
   if (L->lid && !L->wall_z) return -1;
+  /* on-site walls need an inner node next to every boundary node */
+  if (L->onsite && ((L->wall_x && L->nx < 3) || (L->wall_y && L->ny < 3) ||
+                    (L->wall_z && L->nz < 3)))
+    return -1;
   return 0;
 }
 
@@ -169,10 +191,164 @@ static int pull_source(const oracle_lattice *L, int x, int y, int z, int i,
   return 0;
 }
 
+/* ---- on-site velocity boundary (Hecht & Harting), see the header ---- */
+
+/* Solve the 3x3 system A v = r by Gaussian elimination with partial
+ * pivoting. Returns -1 if A is singular. */
+static int solve3(double A[3][3], double r[3], double v[3]) {
+  for (int k = 0; k < 3; ++k) {
+    int p = k;
+    for (int m = k + 1; m < 3; ++m)
+      if (fabs(A[m][k]) > fabs(A[p][k])) p = m;
+    if (fabs(A[p][k]) < 1e-300) return -1;
+    if (p != k) {
+      for (int q = 0; q < 3; ++q) {
+        const double t = A[k][q];
+        A[k][q] = A[p][q];
+        A[p][q] = t;
+      }
+      const double t = r[k];
+      r[k] = r[p];
+      r[p] = t;
+    }
+    for (int m = k + 1; m < 3; ++m) {
+      const double l = A[m][k] / A[k][k];
+      for (int q = k; q < 3; ++q) A[m][q] -= l * A[k][q];
+      r[m] -= l * r[k];
+    }
+  }
+  for (int k = 2; k >= 0; --k) {
+    double s = r[k];
+    for (int q = k + 1; q < 3; ++q) s -= A[k][q] * v[q];
+    v[k] = s / A[k][k];
+  }
+  return 0;
+}
+
+/* Rebuild the unknown populations of gc (unknown[i] = 1) for density rho and
+ * target momentum j (see the header); returns the node's total mass. */
+static double onsite_fill(const int unknown[Q], double rho, const double j[3],
+                          double *gc) {
+  double M[3][3] = {{0}}, r[3], N[3] = {0, 0, 0};
+  for (int a = 0; a < 3; ++a) r[a] = -j[a];
+  int nburied = 0;
+  for (int i = 0; i < Q; ++i) {
+    const int ib = opposite(i);
+    if (!unknown[i]) {
+      for (int a = 0; a < 3; ++a) r[a] += E[i][a] * gc[i];
+    } else if (unknown[ib]) {
+      ++nburied; /* buried: its pair member contributes -e_i b, they cancel */
+    } else {
+      const double ej = E[i][0] * j[0] + E[i][1] * j[1] + E[i][2] * j[2];
+      for (int a = 0; a < 3; ++a) {
+        r[a] += E[i][a] * (gc[ib] + 6.0 * weight(i) * ej);
+        for (int b = 0; b < 3; ++b) M[a][b] += E[i][a] * E[i][b];
+      }
+    }
+  }
+  /* momentum of the rebuilt node: r - M N = 0 */
+  solve3(M, r, N);
+  double mass = 0.0;
+  for (int i = 0; i < Q; ++i) {
+    const int ib = opposite(i);
+    if (unknown[i] && !unknown[ib]) {
+      const double ej = E[i][0] * j[0] + E[i][1] * j[1] + E[i][2] * j[2];
+      const double eN = E[i][0] * N[0] + E[i][1] * N[1] + E[i][2] * N[2];
+      gc[i] = gc[ib] + 6.0 * weight(i) * ej - eN;
+    }
+    if (!(unknown[i] && unknown[ib])) mass += gc[i];
+  }
+  if (nburied) {
+    const double b = (rho - mass) / nburied;
+    for (int i = 0; i < Q; ++i)
+      if (unknown[i] && unknown[opposite(i)]) gc[i] = b;
+    mass = rho;
+  }
+  return mass;
+}
+
+/* Inward normals of the walled faces node (x,y,z) lies on; returns their
+ * count and sums them into s. */
+static int onsite_faces(const oracle_lattice *L, int x, int y, int z, int s[3]) {
+  const int p[3] = {x, y, z}, n[3] = {L->nx, L->ny, L->nz};
+  const int walled[3] = {L->wall_x, L->wall_y, L->wall_z};
+  int count = 0;
+  for (int a = 0; a < 3; ++a) {
+    s[a] = 0;
+    if (!walled[a]) continue;
+    if (p[a] == 0) s[a] = 1;
+    if (p[a] == n[a] - 1) s[a] = -1;
+    count += s[a] != 0;
+  }
+  return count;
+}
+
+/* On-site rule at boundary node (x,y,z): gc holds the pulled populations
+ * (unknown ones are overwritten), f the state before streaming (AoS). */
+static void onsite_node(const oracle_lattice *L, int x, int y, int z,
+                        const int unknown[Q], const double *f,
+                        const double *force, double *gc) {
+  const long n = (long)L->nx * L->ny * L->nz;
+  const long c = ((long)z * L->ny + y) * L->nx + x;
+  int s[3];
+  const int faces = onsite_faces(L, x, y, z, s);
+  double uw[3] = {0.0, 0.0, 0.0}, F[3] = {0.0, 0.0, 0.0};
+  if (L->lid && faces == 1 && z == L->nz - 1)
+    for (int a = 0; a < 3; ++a) uw[a] = L->lid_u[a];
+  if (force)
+    for (int a = 0; a < 3; ++a) F[a] = force[a * n + c];
+  double rho;
+  if (faces == 1) {
+    /* mass = sum g is affine in rho: solve it from two evaluations */
+    double g0[Q], g1[Q], j[3];
+    memcpy(g0, gc, sizeof(g0));
+    memcpy(g1, gc, sizeof(g1));
+    for (int a = 0; a < 3; ++a) j[a] = -0.5 * F[a];
+    const double m0 = onsite_fill(unknown, 0.0, j, g0);
+    for (int a = 0; a < 3; ++a) j[a] = uw[a] - 0.5 * F[a];
+    const double m1 = onsite_fill(unknown, 1.0, j, g1);
+    rho = m0 / (1.0 - (m1 - m0));
+  } else {
+    /* edge or corner: density of the inner diagonal neighbour, stored state */
+    const long nb = ((long)(z + s[2]) * L->ny + (y + s[1])) * L->nx + (x + s[0]);
+    rho = 0.0;
+    for (int i = 0; i < Q; ++i) rho += f[nb * Q + i];
+  }
+  double j[3];
+  for (int a = 0; a < 3; ++a) j[a] = rho * uw[a] - 0.5 * F[a];
+  onsite_fill(unknown, rho, j, gc);
+}
+
+/* Pass 1 with on-site walls: plain pulls where the source is inside, then
+ * the on-site rule on every boundary node. */
+static int stream_onsite(const oracle_lattice *L, const double *f,
+                         const double *force, double *g) {
+  const int nx = L->nx, ny = L->ny, nz = L->nz;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const long c = ((long)z * ny + y) * nx + x;
+        int unknown[Q], any = 0;
+        for (int i = 0; i < Q; ++i) {
+          long src = 0;
+          int lidsrc = 0;
+          unknown[i] = pull_source(L, x, y, z, i, &src, &lidsrc);
+          g[c * Q + i] = unknown[i] ? 0.0 : f[src * Q + i];
+          any |= unknown[i];
+        }
+        if (any) onsite_node(L, x, y, z, unknown, f, force, g + c * Q);
+      }
+  return 0;
+}
+
 /* Pass 1: streaming with the boundary rule (Alg. 3, first loop, then the
- * boundary step). */
-int oracle_stream(const oracle_lattice *L, const double *f, double *g) {
+ * boundary step). The on-site rule uses the body force (its target momentum
+ * is rho u_w - F/2); the halfway rule ignores it. */
+int oracle_stream_forced(const oracle_lattice *L, const double *f,
+                         const double *force, double *g) {
   if (check_lattice(L)) return -1;
+  if (L->onsite) return stream_onsite(L, f, force, g);
   const int nx = L->nx, ny = L->ny, nz = L->nz;
 #pragma omp parallel for collapse(2) schedule(static)
   for (int z = 0; z < nz; ++z)
@@ -195,6 +371,10 @@ int oracle_stream(const oracle_lattice *L, const double *f, double *g) {
         }
       }
   return 0;
+}
+
+int oracle_stream(const oracle_lattice *L, const double *f, double *g) {
+  return oracle_stream_forced(L, f, NULL, g);
 }
 
 /* Pass 2: moments (Eqs. 6-7, with half the force added to the momentum),
@@ -239,7 +419,7 @@ int oracle_run(const oracle_lattice *L, const double *f_in, const double *force,
   }
   memcpy(a, f_in, sizeof(double) * len);
   for (int s = 0; s < nsteps; ++s) {
-    oracle_stream(L, a, g);
+    oracle_stream_forced(L, a, force, g);
     oracle_collide(L, g, force, a);
   }
   memcpy(f_out, a, sizeof(double) * len);
@@ -326,6 +506,7 @@ int oracle_adjoint_step(const oracle_lattice *L, const double *f_n,
                         const double *force, const double *lam_in,
                         double *lam_out, double *grad_force) {
   if (check_lattice(L)) return -1;
+  if (L->onsite) return -1; /* the transpose below is that of the halfway rule */
   const int nx = L->nx, ny = L->ny, nz = L->nz;
   const long n = (long)nx * ny * nz;
   double *g = (double *)malloc(sizeof(double) * n * Q);

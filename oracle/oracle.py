@@ -52,6 +52,7 @@ class _CLattice(ctypes.Structure):
         ("lid", ctypes.c_int),
         ("tau", ctypes.c_double),
         ("lid_u", ctypes.c_double * 3),
+        ("onsite", ctypes.c_int),
     ]
 
 
@@ -75,6 +76,7 @@ def library():
         lib.oracle_set_threads.restype = None
         lib.oracle_init_equilibrium.argtypes = [lp, dp, dp, dp]
         lib.oracle_stream.argtypes = [lp, dp, dp]
+        lib.oracle_stream_forced.argtypes = [lp, dp, dp, dp]
         lib.oracle_collide.argtypes = [lp, dp, dp, dp]
         lib.oracle_run.argtypes = [lp, dp, dp, ctypes.c_int, dp]
         lib.oracle_moments.argtypes = [lp, dp, dp, dp, dp]
@@ -92,7 +94,10 @@ class Lattice:
     ``walls`` is a triple of booleans (x, y, z): a walled axis has halfway
     bounce-back walls at -1/2 and n-1/2, any other axis is periodic.
     ``lid`` (requires a walled z axis) makes the plane z = nz move with
-    velocity ``lid_u``.
+    velocity ``lid_u``. ``onsite`` selects the on-site velocity walls
+    instead: the walls lie on the first and last node planes of each walled
+    axis (at least 3 nodes long), and the lid is the node plane z = nz - 1
+    without its edges.
     """
 
     nx: int
@@ -102,6 +107,7 @@ class Lattice:
     walls: tuple = (False, False, False)
     lid: bool = False
     lid_u: tuple = (0.0, 0.0, 0.0)
+    onsite: bool = False
     _c: _CLattice = field(default=None, repr=False, compare=False)
 
     @property
@@ -120,6 +126,7 @@ class Lattice:
         s.tau = float(self.tau)
         for a in range(3):
             s.lid_u[a] = float(self.lid_u[a])
+        s.onsite = int(bool(self.onsite))
         return s
 
 
@@ -192,14 +199,16 @@ def init_equilibrium(L: Lattice, rho=None, u=None) -> np.ndarray:
     return _soa(f)
 
 
-def stream(L: Lattice, f) -> np.ndarray:
+def stream(L: Lattice, f, force=None) -> np.ndarray:
     """Streaming pass with the boundary rule: g_i(x) = f_i(x - e_i) or its
-    bounce-back replacement."""
+    bounce-back replacement, or for on-site walls the rebuilt unknown
+    populations (whose target momentum rho u_w - F/2 uses the force)."""
     lib = library()
     c = L.c()
     fa = _aos(f)
     g = np.empty_like(fa)
-    _check(lib.oracle_stream(ctypes.byref(c), _dp(fa), _dp(g)), "stream")
+    _check(lib.oracle_stream_forced(ctypes.byref(c), _dp(fa), _dp(_vec(force, L)), _dp(g)),
+           "stream")
     return _soa(g)
 
 

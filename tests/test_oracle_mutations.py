@@ -32,6 +32,14 @@ MUTANTS = {
     "moments_without_half_force": (
         "u[a * n + c] = (m[a] - 0.5 * F) / r;", "u[a * n + c] = (m[a]) / r;"),
     "lid_on_wrong_plane": ("sz == L->nz);", "sz < 0);"),
+    "onsite_transverse_correction_dropped": ("  solve3(M, r, N);", "  if (0) solve3(M, r, N);"),
+    "onsite_half_force_sign": ("j[a] = rho * uw[a] - 0.5 * F[a];",
+                               "j[a] = rho * uw[a] + 0.5 * F[a];"),
+    "onsite_edge_density_from_the_node_itself": ("rho += f[nb * Q + i];", "rho += f[c * Q + i];"),
+    "onsite_lid_on_top_edges": ("if (L->lid && faces == 1 && z == L->nz - 1)",
+                                "if (L->lid && z == L->nz - 1)"),
+    "onsite_rebuild_weight": ("gc[i] = gc[ib] + 6.0 * weight(i) * ej - eN;",
+                              "gc[i] = gc[ib] + 3.0 * weight(i) * ej - eN;"),
 }
 
 
@@ -47,6 +55,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     (tmp_path / "pytest.ini").write_text("[pytest]\nmarkers =\n    gpu: gpu\n    slow: slow\n")
     r = subprocess.run(
         [sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-         "tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py"],
+         "tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py",
+         "tests/test_oracle_onsite.py"],
         cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1 and " failed" in r.stdout, r.stdout[-2000:] + r.stderr[-2000:]
