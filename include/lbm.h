@@ -78,6 +78,23 @@ extern "C" {
 #define LBM_STORE_BF16 0x20u /* ... as BF16, round to nearest even (76 B) */
 #define LBM_FORCE 0x40u      /* read a per-cell body force F each step */
 #define LBM_ADJOINT 0x80u    /* the handle will run the adjoint (FP32 storage only) */
+/* LBM_WALLS_ONSITE: walled axes use the on-site velocity condition the paper
+ * used for its cavity (Sec. 5: Hecht & Harting's D3Q19 on-site conditions)
+ * instead of halfway bounce-back. The walls then lie ON the first and last
+ * node planes of each walled axis (at least 3 nodes long, else LBM_EINVAL).
+ * Those nodes stream and collide like any other; after the pull, the
+ * populations they would take from outside the lattice are rebuilt so that
+ * the node's velocity (sum e g + F/2)/rho is exactly the wall velocity:
+ * non-equilibrium bounce-back along the normal plus a transverse momentum
+ * correction, the density fixed by mass on a face. On edges and corners the
+ * density is the inner diagonal neighbour's (stored state of the previous
+ * step) and opposite populations that both point along the walls share the
+ * remaining mass equally. With LBM_LID the interior of the top plane
+ * z = nz - 1 moves with the lid velocity; its edges and every other wall
+ * node are at rest. Runs on LBM_KERNEL_X2 and LBM_KERNEL_NODE; the adjoint,
+ * lbm_step_push, lbm_stream and the batched path keep halfway walls only
+ * (LBM_EINVAL with this flag). */
+#define LBM_WALLS_ONSITE 0x100u
 #define LBM_CAVITY (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z | LBM_LID)
 
 typedef struct lbm_lattice lbm_t;

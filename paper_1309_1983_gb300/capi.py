@@ -34,6 +34,7 @@ LBM_STORE_F16 = 0x10
 LBM_STORE_BF16 = 0x20
 LBM_FORCE = 0x40
 LBM_ADJOINT = 0x80
+LBM_WALLS_ONSITE = 0x100
 LBM_BUF_F, LBM_BUF_FORCE, LBM_BUF_RHO, LBM_BUF_U, LBM_BUF_LAMBDA, LBM_BUF_GRADF = range(6)
 LBM_CAVITY = LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z | LBM_LID
 LBM_WALLS_AUTO = 0

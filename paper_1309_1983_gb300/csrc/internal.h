@@ -25,6 +25,9 @@ struct StepArgs {
   float lidc[19];      // 6 w_i (e_i . u_w) for sources on z = nz (else 0)
   int z0, zn;          // planes [z0, z0 + zn) processed by a launch (0, nz: all)
   int wall_select;     // 1: per-direction address select, 0: branch on wall nodes
+  int onsite;          // 1: walled axes use the on-site velocity rule (onsite.cuh)
+  int onsite_lid;      // 1: the top plane's interior moves with lid[] (on-site)
+  float lid[3];        // lid velocity u_w
 };
 
 struct Scratch {

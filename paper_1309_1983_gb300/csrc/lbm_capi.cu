@@ -69,7 +69,12 @@ int cuda_fail(cudaError_t e, const char *where) {
 
 constexpr uint32_t kKnownFlags = LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z |
                                  LBM_LID | LBM_STORE_F16 | LBM_STORE_BF16 |
-                                 LBM_FORCE | LBM_ADJOINT;
+                                 LBM_FORCE | LBM_ADJOINT | LBM_WALLS_ONSITE;
+
+// On-site walls on a handle that has a walled axis.
+bool onsite(const lbm_t *h) {
+  return (h->flags & LBM_WALLS_ONSITE) && (h->flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z));
+}
 
 StepArgs make_args(const lbm_t *h, const void *fin, void *fout) {
   StepArgs a;
@@ -93,6 +98,9 @@ StepArgs make_args(const lbm_t *h, const void *fin, void *fout) {
   // (long rows). FP32 is bandwidth-bound and the divergence-free select form
   // is never slower; the two-node kernel selects only in the warps that hold
   // a wall node and is fastest so.
+  a.onsite = onsite(h) ? 1 : 0;
+  a.onsite_lid = (h->flags & LBM_LID) ? 1 : 0;
+  for (int k = 0; k < 3; ++k) a.lid[k] = h->lid[k];
   a.wall_select = h->wall_mode == LBM_WALLS_SELECT ||
                   (h->wall_mode == LBM_WALLS_AUTO &&
                    (h->storage == lbm::kF32 || h->nx < 256 || h->kernel == LBM_KERNEL_X2));
@@ -318,6 +326,12 @@ int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
   if ((flags & LBM_LID) && !(flags & LBM_WALL_Z))
     return fail(LBM_EINVAL, "LBM_LID needs LBM_WALL_Z");
   if ((flags & LBM_ADJOINT) && st) return fail(LBM_EINVAL, "LBM_ADJOINT needs FP32 storage");
+  if (flags & LBM_WALLS_ONSITE) {
+    if (((flags & LBM_WALL_X) && nx < 3) || ((flags & LBM_WALL_Y) && ny < 3) ||
+        ((flags & LBM_WALL_Z) && nz < 3))
+      return fail(LBM_EINVAL, "on-site walls need >= 3 nodes along every walled axis");
+    if (flags & LBM_ADJOINT) return fail(LBM_EINVAL, "the adjoint supports halfway walls only");
+  }
   const int storage = st == LBM_STORE_F16 ? lbm::kF16
                       : st == LBM_STORE_BF16 ? lbm::kBF16 : lbm::kF32;
   const int eb = storage == lbm::kF32 ? 4 : 2;
@@ -464,6 +478,8 @@ int lbm_set_kernel(lbm_t *h, int variant) {
     return fail(LBM_EINVAL, "unknown kernel variant");
   if (variant == LBM_KERNEL_PAIR && h->storage == lbm::kF32)
     return fail(LBM_EINVAL, "the shuffle pair kernel needs 16-bit storage");
+  if (onsite(h) && variant != LBM_KERNEL_X2 && variant != LBM_KERNEL_NODE)
+    return fail(LBM_EINVAL, "on-site walls run on LBM_KERNEL_X2 or LBM_KERNEL_NODE");
   h->kernel = variant;
   h->config_version++;
   return LBM_OK;
@@ -560,6 +576,7 @@ int lbm_step_push(lbm_t *h, const void *g_in, void *g_out) {
   if (!g_in || !g_out || g_in == g_out) return fail(LBM_EINVAL, "bad buffers");
   if (!aligned(g_in, 256) || !aligned(g_out, 256))
     return fail(LBM_EINVAL, "buffers must be 256-byte aligned");
+  if (onsite(h)) return fail(LBM_EINVAL, "the push iteration supports halfway walls only");
   StepArgs a = make_args(h, g_in, g_out);
   cudaError_t e = lbm::launch_step_push(h->storage, a, h->bx, h->by, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "push step launch");
@@ -573,6 +590,7 @@ int lbm_stream(lbm_t *h, const void *f_in, void *f_out, int form) {
   if (form < LBM_STREAM_PULL || form > LBM_STREAM_COPY) return fail(LBM_EINVAL, "bad form");
   if (!aligned(f_in, 256) || !aligned(f_out, 256))
     return fail(LBM_EINVAL, "buffers must be 256-byte aligned");
+  if (onsite(h)) return fail(LBM_EINVAL, "streaming alone supports halfway walls only");
   StepArgs a = make_args(h, f_in, f_out);
   cudaError_t e = lbm::launch_stream(h->storage, a, form, h->bx, h->by, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "stream kernel launch");
@@ -815,6 +833,7 @@ int lbm_adjoint_step(lbm_t *h, const void *f_n, const float *lambda_in,
   if (h->storage != lbm::kF32) return fail(LBM_EINVAL, "adjoint needs FP32 storage");
   if (!f_n || !lambda_in || !lambda_out || lambda_in == lambda_out)
     return fail(LBM_EINVAL, "bad buffers");
+  if (onsite(h)) return fail(LBM_EINVAL, "the adjoint supports halfway walls only");
   StepArgs g = make_args(h, f_n, nullptr);
   // The adjoint issues ~1.7x the forward's instructions per node: the branch
   // form (fewer instructions off the walls) wins from 64-node rows on
@@ -836,6 +855,7 @@ int lbm_adjoint_step_moments(lbm_t *h, const float *rho_n, const float *u_n,
   if (h->storage != lbm::kF32) return fail(LBM_EINVAL, "adjoint needs FP32 storage");
   if (!rho_n || !u_n || !lambda_in || !lambda_out || lambda_in == lambda_out)
     return fail(LBM_EINVAL, "bad buffers");
+  if (onsite(h)) return fail(LBM_EINVAL, "the adjoint supports halfway walls only");
   StepArgs g = make_args(h, nullptr, nullptr);
   g.wall_select = h->wall_mode == LBM_WALLS_SELECT ||
                   (h->wall_mode == LBM_WALLS_AUTO && h->nx < 64);

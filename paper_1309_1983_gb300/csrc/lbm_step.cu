@@ -13,6 +13,7 @@
 // neighbouring warps still pull.
 #include "d3q19.cuh"
 #include "internal.h"
+#include "onsite.cuh"
 #include "stream.cuh"
 
 namespace lbm {
@@ -29,7 +30,8 @@ namespace lbm {
 
 // W: 0 periodic, 1 walls by address selection, 2 walls by the wall-node
 // branch (separate kernels: compiling both wall forms into one kernel cost
-// ~50 instructions per node even though only one runs).
+// ~50 instructions per node even though only one runs), 3 on-site velocity
+// walls (plain pull, then the rule of onsite.cuh on wall nodes).
 template <int S, int W, bool FORCE, bool MOM>
 __global__ void LBM_STEP_BOUNDS k_step(const StepArgs a) {
   using T = typename Store<S>::T;
@@ -37,10 +39,38 @@ __global__ void LBM_STEP_BOUNDS k_step(const StepArgs a) {
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = a.z0 + blockIdx.z;
   if (x >= a.nx || y >= a.ny) return;
-  step_node<S, (W != 0), FORCE, MOM, false>(
-      static_cast<const T *>(a.fin), static_cast<T *>(a.fout), a.nx, a.ny, a.nz, a.pitch,
-      a.plane, a.walls, a.lidc, a.omega, a.kf, a.force, a.rho, a.u, a.cells, x, y, z,
-      W == 1);
+  if constexpr (W == 3) {
+    const T *__restrict__ fin = static_cast<const T *>(a.fin);
+    T *__restrict__ fout = static_cast<T *>(a.fout);
+    const NodeIdx n = node_index(a.nx, a.ny, a.nz, a.pitch, a.walls, x, y, z);
+    float d[Q];
+    gather<S>(fin, a.plane, n, d);
+    const uint32_t dc = ((uint32_t)z * a.ny + y) * a.nx + x;
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    if constexpr (FORCE) {
+      Fx = __ldg(a.force + dc);
+      Fy = __ldg(a.force + a.cells + dc);
+      Fz = __ldg(a.force + 2 * (size_t)a.cells + dc);
+    }
+    if (on_wall(n)) onsite_apply<S>(fin, a, n, Fx, Fy, Fz, d);
+    float rho, ux, uy, uz;
+    collide<FORCE>(d, a.omega, a.kf, Fx, Fy, Fz, rho, ux, uy, uz);
+    static_for<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      Store<S>::st(fout + (size_t)i * a.plane + n.c, d[i]);
+    });
+    if constexpr (MOM) {
+      a.rho[dc] = rho;
+      a.u[dc] = ux;
+      a.u[a.cells + dc] = uy;
+      a.u[2 * (size_t)a.cells + dc] = uz;
+    }
+  } else {
+    step_node<S, (W != 0), FORCE, MOM, false>(
+        static_cast<const T *>(a.fin), static_cast<T *>(a.fout), a.nx, a.ny, a.nz, a.pitch,
+        a.plane, a.walls, a.lidc, a.omega, a.kf, a.force, a.rho, a.u, a.cells, x, y, z,
+        W == 1);
+  }
 }
 
 template <int S>
@@ -152,7 +182,7 @@ static dim3 node_grid(const StepArgs &a, int bx, int by) {
 template <int S>
 static void step_dispatch(bool moments, const StepArgs &a, dim3 g, dim3 b,
                           cudaStream_t s) {
-  const int walls = a.walls == 0 ? 0 : a.wall_select ? 1 : 2;
+  const int walls = a.walls == 0 ? 0 : a.onsite ? 3 : a.wall_select ? 1 : 2;
   const bool force = a.force != nullptr;
 #define LBM_STEP_CASE(W, F, M)                                  \
   if (walls == W && force == F && moments == M) {               \
@@ -171,6 +201,10 @@ static void step_dispatch(bool moments, const StepArgs &a, dim3 g, dim3 b,
   LBM_STEP_CASE(2, false, true)
   LBM_STEP_CASE(2, true, false)
   LBM_STEP_CASE(2, true, true)
+  LBM_STEP_CASE(3, false, false)
+  LBM_STEP_CASE(3, false, true)
+  LBM_STEP_CASE(3, true, false)
+  LBM_STEP_CASE(3, true, true)
 #undef LBM_STEP_CASE
 }
 

@@ -25,6 +25,7 @@
 
 #include "d3q19.cuh"
 #include "internal.h"
+#include "onsite.cuh"
 #include "stream.cuh"
 
 namespace lbm {
@@ -123,7 +124,8 @@ __device__ __forceinline__ void pull_pair(const typename Store<S>::T *__restrict
 // node (a warp vote picks the plain periodic pulls for the others: no
 // divergence, and 5-14% faster than selecting in every warp), 2 walls by the
 // wall-node branch (the one-node kernel's face fix-ups, per node of the
-// pair).
+// pair), 3 on-site velocity walls (plain pulls, then the rule of onsite.cuh
+// on each wall node of the pair).
 template <int S, int W, bool FORCE, bool MOM>
 __global__ void LBM_X2_BOUNDS k_step_x2(const StepArgs a) {
   using T = typename Store<S>::T;
@@ -175,6 +177,10 @@ __global__ void LBM_X2_BOUNDS k_step_x2(const StepArgs a) {
       F1z = __ldg(a.force + 2 * (size_t)a.cells + dc + 1);
     }
   }
+  if constexpr (W == 3) {
+    if (on_wall(n0)) onsite_apply<S>(fin, a, n0, F0x, F0y, F0z, d0);
+    if (has1 && on_wall(n1)) onsite_apply<S>(fin, a, n1, F1x, F1y, F1z, d1);
+  }
   float r0, u0x, u0y, u0z, r1, u1x, u1y, u1z;
   collide<FORCE>(d0, a.omega, a.kf, F0x, F0y, F0z, r0, u0x, u0y, u0z);
   collide<FORCE>(d1, a.omega, a.kf, F1x, F1y, F1z, r1, u1x, u1y, u1z);
@@ -198,7 +204,7 @@ __global__ void LBM_X2_BOUNDS k_step_x2(const StepArgs a) {
 
 template <int S>
 static void x2_dispatch(bool moments, const StepArgs &a, dim3 g, dim3 b, cudaStream_t s) {
-  const int walls = a.walls == 0 ? 0 : a.wall_select ? 1 : 2;
+  const int walls = a.walls == 0 ? 0 : a.onsite ? 3 : a.wall_select ? 1 : 2;
   const bool force = a.force != nullptr;
 #define LBM_X2_CASE(W, F, M)                                    \
   if (walls == W && force == F && moments == M) {               \
@@ -217,6 +223,10 @@ static void x2_dispatch(bool moments, const StepArgs &a, dim3 g, dim3 b, cudaStr
   LBM_X2_CASE(2, false, true)
   LBM_X2_CASE(2, true, false)
   LBM_X2_CASE(2, true, true)
+  LBM_X2_CASE(3, false, false)
+  LBM_X2_CASE(3, false, true)
+  LBM_X2_CASE(3, true, false)
+  LBM_X2_CASE(3, true, true)
 #undef LBM_X2_CASE
 }
 

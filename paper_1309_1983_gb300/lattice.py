@@ -30,10 +30,12 @@ class Lattice:
     z = nz (needs a z wall), or None. ``storage``: "f32", "f16" or "bf16".
     ``force``: True to allocate a per-cell body force field
     (:attr:`force`, shape (3, nz, ny, nx), zero-initialised).
+    ``onsite``: True for on-site velocity walls (LBM_WALLS_ONSITE) instead
+    of halfway bounce-back.
     """
 
     def __init__(self, nx, ny, nz, tau, walls=(False, False, False), lid=None,
-                 storage="f32", force=False, device="cuda", stream=None):
+                 storage="f32", force=False, device="cuda", stream=None, onsite=False):
         flags = 0
         if walls[0]:
             flags |= capi.LBM_WALL_X
@@ -46,6 +48,8 @@ class Lattice:
         flags |= _STORAGE[storage]
         if force:
             flags |= capi.LBM_FORCE
+        if onsite:
+            flags |= capi.LBM_WALLS_ONSITE
         self.nx, self.ny, self.nz = nx, ny, nz
         self.tau = float(tau)
         self.storage = storage

@@ -44,6 +44,10 @@ def test_strerror_names_every_code(lib):
     ((4, 4, 4, 0.8, capi.LBM_STORE_F16 | capi.LBM_STORE_BF16), capi.LBM_EINVAL),
     ((4, 4, 4, 0.8, 0x1000), capi.LBM_EINVAL),
     ((2048, 2048, 1024, 0.8, 0), capi.LBM_ERANGE),
+    # on-site walls need 3 nodes along every walled axis, and no adjoint
+    ((4, 2, 4, 0.8, capi.LBM_WALLS_ONSITE | capi.LBM_WALL_Y), capi.LBM_EINVAL),
+    ((4, 4, 4, 0.8, capi.LBM_WALLS_ONSITE | capi.LBM_CAVITY | capi.LBM_ADJOINT),
+     capi.LBM_EINVAL),
 ])
 def test_create_rejects_bad_arguments(lib, args, code):
     h = ctypes.c_void_p()
@@ -193,3 +197,22 @@ def test_kernel_variants_need_matching_storage(lib):
     finally:
         lib.lbm_destroy(h32)
         lib.lbm_destroy(h16)
+
+
+def test_onsite_handles_reject_kernels_without_the_rule(lib):
+    """On-site walls run on the two-node and one-node kernels only; the
+    choice is checked on the host (no CUDA call)."""
+    h = capi.create(8, 8, 8, 0.8, capi.LBM_WALLS_ONSITE | capi.LBM_CAVITY)
+    try:
+        for k in (capi.LBM_KERNEL_BULK, capi.LBM_KERNEL_BULK1):
+            assert lib.lbm_set_kernel(h, k) == capi.LBM_EINVAL
+        for k in (capi.LBM_KERNEL_NODE, capi.LBM_KERNEL_X2):
+            assert lib.lbm_set_kernel(h, k) == capi.LBM_OK
+    finally:
+        lib.lbm_destroy(h)
+    # without a walled axis the flag changes nothing
+    h = capi.create(8, 8, 8, 0.8, capi.LBM_WALLS_ONSITE)
+    try:
+        assert lib.lbm_set_kernel(h, capi.LBM_KERNEL_BULK) == capi.LBM_OK
+    finally:
+        lib.lbm_destroy(h)
