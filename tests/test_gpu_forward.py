@@ -214,9 +214,9 @@ def test_step_to_matches_step():
     out = torch.empty_like(cur)
     L.step_to(cur, out)
     L.step(1)
-    cur2, _ = L.current_buffers()
     torch.cuda.synchronize()
-    assert torch.equal(out, cur2)
+    # node elements only: row padding (here the x walls' ghost slots) is not state
+    np.testing.assert_array_equal(L.buffer_to_numpy(out), L.get_f())
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
