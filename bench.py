@@ -481,7 +481,7 @@ def batch_workload(torch, steps=2000):
         L.close()
     del lats
     torch.cuda.empty_cache()
-    adj = batch_adjoint_workload(torch, G, steps)
+    adj = batch_adjoint_workload(torch, G, steps, tiling=tiling[:2])
     return {"domains": 64, "cells": cells, "steps": steps, "forward_plus_adjoint": adj,
             "persistent_mlups": round(cells * steps / ms / 1e3, 1),
             "tile_launch_per_step_mlups": round(cells * 200 / ms_launch / 1e3, 1),
@@ -491,14 +491,18 @@ def batch_workload(torch, steps=2000):
             "grid": info["grid"], "graph": info["graph"]}
 
 
-def batch_adjoint_workload(torch, G, T, K=50):
+def batch_adjoint_workload(torch, G, T, K=50, tiling=None):
     """Forward plus adjoint over the same 64 cavities: start at rest, T steps
-    (one launch per step, checkpoints every K), loss against a seeded target
-    velocity in every domain, gradients with respect to u0 and F (at F = 0)."""
+    (checkpoints every K), loss against a seeded target velocity in every
+    domain, gradients with respect to u0 and F (at F = 0). Every K-step
+    forward segment, segment recompute and reverse sweep is one persistent
+    launch (lbm_batch_run, lbm_batch_adjoint_run) with the forward's tiling."""
     from paper_1309_1983_gb300 import workloads as W
     from paper_1309_1983_gb300.adjoint import BatchAdjointProblem
     from paper_1309_1983_gb300.batch import Batch
     B = Batch(G.dims, G.tau, G.lid_u)
+    if tiling:
+        B.set_tiling(*tiling)
     P = BatchAdjointProblem(B, T, K)
     ut = B.pack_vectors([W.separable_modes(int(d[0]), int(d[1]), int(d[2]), seed=2 + k,
                                            amp=0.02)

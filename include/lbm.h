@@ -492,6 +492,29 @@ int lbm_batch_adjoint_step_moments(lbm_batch_t *b, const float *rho_n, const flo
 int lbm_batch_adjoint_u0(lbm_batch_t *b, const float *lambda0, const float *u0,
                          float *grad_u0);
 
+/* Step sequences in ONE persistent cooperative launch each (a grid barrier
+ * with bounded waits between steps, replayed from a cached CUDA graph), for
+ * the checkpointed adjoint's forward segments, segment recompute and
+ * reverse sweeps. Both wait for the launch; LBM_ETIMEOUT as lbm_batch_step.
+ *
+ * lbm_batch_run: n in [1, 64] steps; step k reads f_in[k] and writes
+ * f_out[k] (device buffers in the batch layout, f_in[k] != f_out[k]; step
+ * k + 1 sees step k's output only if f_in[k + 1] = f_out[k]). rho and u:
+ * both NULL, or arrays of n dense field buffers that step k's collision
+ * writes (as lbm_batch_step_to_moments). The bound pair is not touched.
+ *
+ * lbm_batch_adjoint_run: n in [1, 64] reverse steps from stored moments
+ * (as lbm_batch_adjoint_step_moments): step k reads lambda from lambda_a
+ * (k even) or lambda_b (k odd) and writes the other, with rho[k], u[k] the
+ * moments of the forward step it reverses (so the caller lists them from
+ * the last forward step backwards). After n steps lambda^0 of the sequence
+ * is in lambda_a if n is even, else in lambda_b. grad_force: NULL or the
+ * dense field the force cotangent is ADDED into. */
+int lbm_batch_run(lbm_batch_t *b, int n, const void *const *f_in, void *const *f_out,
+                  float *const *rho, float *const *u);
+int lbm_batch_adjoint_run(lbm_batch_t *b, int n, const float *const *rho, const float *const *u,
+                          float *lambda_a, float *lambda_b, float *grad_force);
+
 /* rho and u of every node of the current state into dense device fields
  * (layout above); either may be NULL. */
 int lbm_batch_moments(lbm_batch_t *b, float *rho, float *u);

@@ -80,6 +80,23 @@ class _Checkpointed:
     def _field(self):
         raise NotImplementedError
 
+    # -- step sequences: one call per step unless a subclass runs them in bulk --
+    def _run(self, fins, fouts):
+        for fin, fout in zip(fins, fouts):
+            self._step_to(fin, fout)
+
+    def _run_mom(self, fins, fouts, moms):
+        for fin, fout, (rho, u) in zip(fins, fouts, moms):
+            self._step_mom(fin, fout, rho, u)
+
+    def _reverse(self, moms, lam_a, lam_b, gF):
+        """Reverse steps over moms (last forward step first), lambda^{n+1} in
+        lam_a; returns (lambda^n, the other buffer)."""
+        for rho, u in moms:
+            self._adj_step_mom(rho, u, lam_a, lam_b, gF)
+            lam_a, lam_b = lam_b, lam_a
+        return lam_a, lam_b
+
     # -- driver -------------------------------------------------------------------
     def forward(self, u0, F):
         """f^0 = f^eq(1, u0), then T steps keeping every K-th state.
@@ -90,6 +107,7 @@ class _Checkpointed:
         f0 = self._init(u0, F)
         ckpts = [f0]
         prev = f0
+        fins, fouts = [], []
         for n in range(1, self.T + 1):
             if n % self.K == 0 and n < self.T:
                 c = len(ckpts) - 1  # checkpoint buffers are reused across calls
@@ -99,8 +117,12 @@ class _Checkpointed:
                 ckpts.append(dst)
             else:
                 dst = self._scratch[n % 2]
-            self._step_to(prev, dst)
+            fins.append(prev)
+            fouts.append(dst)
             prev = dst
+            if n % self.K == 0 or n == self.T:  # one segment per call
+                self._run(fins, fouts)
+                fins, fouts = [], []
         return prev, ckpts
 
     def backward(self, f_T, ckpts, u0, ut):
@@ -122,14 +144,11 @@ class _Checkpointed:
             stop = min(start + self.K, self.T)
             if self.moments:
                 # f_T (a scratch buffer) is no longer needed after the seed
-                cur = ckpts[s]
-                for k in range(stop - start):
-                    dst = self._scratch[k % 2]
-                    self._step_mom(cur, dst, *self._mom_seg[k])
-                    cur = dst
-                for n in range(stop - 1, start - 1, -1):
-                    self._adj_step_mom(*self._mom_seg[n - start], lam_a, lam_b, gF)
-                    lam_a, lam_b = lam_b, lam_a
+                m = stop - start
+                fins = [ckpts[s]] + [self._scratch[k % 2] for k in range(m - 1)]
+                fouts = [self._scratch[k % 2] for k in range(m)]
+                self._run_mom(fins, fouts, self._mom_seg[:m])
+                lam_a, lam_b = self._reverse(self._mom_seg[:m][::-1], lam_a, lam_b, gF)
                 continue
             states = [ckpts[s]]
             for k in range(1, stop - start):
@@ -266,6 +285,36 @@ class BatchAdjointProblem(_Checkpointed):
 
     def _field(self):
         return torch.empty(3 * self.b.cells, dtype=torch.float32, device=self.device)
+
+    # segments, recompute and reverse sweeps as persistent launches of up to
+    # 64 steps each (lbm_batch_run, lbm_batch_adjoint_run)
+    _CHUNK = 64
+
+    @staticmethod
+    def _ptrs(ts):
+        return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+    def _run(self, fins, fouts):
+        for k in range(0, len(fins), self._CHUNK):
+            fi, fo = fins[k:k + self._CHUNK], fouts[k:k + self._CHUNK]
+            capi.call("lbm_batch_run", self.b.handle, len(fi), self._ptrs(fi), self._ptrs(fo),
+                      None, None)
+
+    def _run_mom(self, fins, fouts, moms):
+        for k in range(0, len(fins), self._CHUNK):
+            fi, fo, mm = fins[k:k + self._CHUNK], fouts[k:k + self._CHUNK], moms[k:k + self._CHUNK]
+            capi.call("lbm_batch_run", self.b.handle, len(fi), self._ptrs(fi), self._ptrs(fo),
+                      self._ptrs([r for r, _ in mm]), self._ptrs([u for _, u in mm]))
+
+    def _reverse(self, moms, lam_a, lam_b, gF):
+        for k in range(0, len(moms), self._CHUNK):
+            mm = moms[k:k + self._CHUNK]
+            capi.call("lbm_batch_adjoint_run", self.b.handle, len(mm),
+                      self._ptrs([r for r, _ in mm]), self._ptrs([u for _, u in mm]),
+                      _p(lam_a), _p(lam_b), _p(gF))
+            if len(mm) % 2:
+                lam_a, lam_b = lam_b, lam_a
+        return lam_a, lam_b
 
 
 class VelocityMismatch(torch.autograd.Function):

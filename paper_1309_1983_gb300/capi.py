@@ -131,6 +131,8 @@ _SIGNATURES = {
     "lbm_batch_adjoint_step": [_vp, _vp, _vp, _vp, _vp],
     "lbm_batch_adjoint_step_moments": [_vp, _vp, _vp, _vp, _vp, _vp],
     "lbm_batch_adjoint_u0": [_vp, _vp, _vp, _vp],
+    "lbm_batch_run": [_vp, _i, _vp, _vp, _vp, _vp],
+    "lbm_batch_adjoint_run": [_vp, _i, _vp, _vp, _vp, _vp, _vp],
 }
 _RESTYPE = {"lbm_strerror": ctypes.c_char_p, "lbm_last_error": ctypes.c_char_p}
 

@@ -74,12 +74,16 @@ __device__ __forceinline__ bool warp_has_wall(const NodeIdx &n) {
   return __any_sync(__activemask(), on_wall(n));
 }
 
-// lambda^{n+1} at the node (aligned loads).
+// lambda^{n+1} at the node (aligned loads). L2ONLY: through L2 only
+// (ld.global.cg), for persistent kernels in which other blocks wrote
+// lambda^{n+1} before the last grid barrier.
+template <bool L2ONLY = false>
 __device__ __forceinline__ void load_lambda(const float *__restrict__ lam_in, uint32_t plane,
                                             const NodeIdx &n, float (&lam)[Q]) {
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    lam[i] = __ldg(lam_in + (size_t)i * plane + n.c);
+    lam[i] = L2ONLY ? __ldcg(lam_in + (size_t)i * plane + n.c)
+                    : __ldg(lam_in + (size_t)i * plane + n.c);
   });
 }
 
@@ -196,7 +200,7 @@ __device__ __forceinline__ void adjoint_node(
 // One reverse step at node (x, y, z) from the moments rho^n, u^n that the
 // forward step's collision used (dense fields, as lbm_step_moments writes
 // them): no gather of f^n, 16 bytes per node instead of 76.
-template <bool WALLS, bool FORCE, bool GRADF>
+template <bool WALLS, bool FORCE, bool GRADF, bool L2ONLY = false>
 __device__ __forceinline__ void adjoint_node_mom(
     const float *__restrict__ rho_n, const float *__restrict__ u_n,
     const float *__restrict__ lam_in, float *__restrict__ lam_out,
@@ -217,7 +221,7 @@ __device__ __forceinline__ void adjoint_node_mom(
   const float uy = __ldg(u_n + cells + dc);
   const float uz = __ldg(u_n + 2 * (size_t)cells + dc);
   float lam[Q];
-  load_lambda(lam_in, plane, n, lam);
+  load_lambda<L2ONLY>(lam_in, plane, n, lam);
   adjoint_core<FORCE, GRADF>(lam, lam_out, gF, plane, n, sel, dc, cells, rho, ux, uy, uz, Fx,
                              Fy, Fz, omega, kf);
 }

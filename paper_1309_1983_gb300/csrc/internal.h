@@ -105,6 +105,27 @@ struct BatchDom {
   float lidc[19];
 };
 
+// Steps of one persistent batched launch (lbm_batch_run /
+// lbm_batch_adjoint_run): per step its input and output f buffers and,
+// optionally, the dense rho / u fields the step's collision writes.
+constexpr int kMaxSeqSteps = 64;
+struct BatchFwdSeq {
+  int n;
+  const float *fin[kMaxSeqSteps];
+  float *fout[kMaxSeqSteps];
+  float *rho[kMaxSeqSteps];
+  float *u[kMaxSeqSteps];
+};
+// Reverse steps from stored moments: step s reads lam[s & 1] and writes
+// lam[(s & 1) ^ 1], with the moments of the forward step it reverses.
+struct BatchAdjSeq {
+  int n;
+  float *lam[2];
+  float *gF;
+  const float *rho[kMaxSeqSteps];
+  const float *u[kMaxSeqSteps];
+};
+
 struct BatchArgs {
   float *f[2];
   const BatchDom *doms;
@@ -135,6 +156,14 @@ cudaError_t launch_batch_persistent(const BatchArgs &a, int grid, int threads,
                                     cudaStream_t s);
 cudaError_t launch_batch_step(const BatchArgs &a, const float *fin, float *fout,
                               int threads, cudaStream_t s);
+// Persistent cooperative launches of a step sequence (grid barrier between
+// steps); the kernels behind them for the occupancy query.
+const void *batch_fwd_seq_kernel(bool walls, bool moments);
+const void *batch_adj_seq_kernel(bool gradf);
+cudaError_t launch_batch_fwd_seq(const BatchArgs &a, const BatchFwdSeq &q, int grid, int threads,
+                                 cudaStream_t s);
+cudaError_t launch_batch_adj_seq(const BatchArgs &a, const BatchAdjSeq &q, int grid, int threads,
+                                 cudaStream_t s);
 cudaError_t launch_batch_step_mom(const BatchArgs &a, const float *fin, float *fout, float *rho,
                                   float *u, int threads, cudaStream_t s);
 cudaError_t launch_batch_adjoint_step_mom(const BatchArgs &a, const float *rho, const float *u,

@@ -120,6 +120,93 @@ __global__ void __launch_bounds__(256) k_batch_persistent(const BatchArgs a) {
   }
 }
 
+// Copy the domain table into shared memory (once per persistent launch).
+__device__ __forceinline__ BatchDom *stage_domains(const BatchArgs &a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BatchDom *sdoms = reinterpret_cast<BatchDom *>(smem_raw);
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(a.doms);
+  uint32_t *dst = reinterpret_cast<uint32_t *>(sdoms);
+  const int words = a.ndom * (int)(sizeof(BatchDom) / 4);
+  for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+  return sdoms;
+}
+
+// A sequence of q.n steps, each from its own input buffer into its own
+// output buffer (and, with MOM, writing the collision's rho and u), in one
+// persistent launch: the forward segments and the segment recompute of the
+// checkpointed adjoint. Tiles, prefetch, L2-only loads and the bounded grid
+// barrier as in k_batch_persistent. The step table is a __grid_constant__
+// parameter, so indexing it by the step number needs no local copy.
+template <bool WALLS, bool MOM>
+__global__ void __launch_bounds__(256) k_batch_fwd_seq(const BatchArgs a,
+                                                       const __grid_constant__ BatchFwdSeq q) {
+  const BatchDom *sdoms = stage_domains(a);
+  for (int s = 0; s < q.n; ++s) {
+    const float *fin = q.fin[s];
+    float *fout = q.fout[s];
+    float *rho = MOM ? q.rho[s] : nullptr;
+    float *u = MOM ? q.u[s] : nullptr;
+    int t = blockIdx.x;
+    int2 tile = t < a.ntiles ? a.tiles[t] : make_int2(0, 0);
+    for (; t < a.ntiles; t += gridDim.x) {
+      const int tn = t + gridDim.x;
+      const int2 next = tn < a.ntiles ? a.tiles[tn] : tile;
+      const BatchDom &D = sdoms[tile.x];
+      const uint32_t k = (uint32_t)tile.y + threadIdx.x;
+      if (k < D.cells) {
+        int x, y, z;
+        decode(D, k, x, y, z);
+        step_node<0, WALLS, false, MOM, true>(
+            fin + D.foff, fout + D.foff, D.nx, D.ny, D.nz, D.pitch, D.plane, D.walls, D.lidc,
+            D.omega, D.kf, nullptr, MOM ? rho + D.coff : nullptr,
+            MOM ? u + 3 * (size_t)D.coff : nullptr, D.cells, x, y, z);
+      }
+      tile = next;
+    }
+    if (s + 1 < q.n && !grid_barrier(a)) return;
+  }
+}
+
+// q.n reverse steps from stored moments in one persistent launch: step s
+// reads lambda from q.lam[s & 1] (through L2: other blocks scattered it
+// before the barrier) and writes q.lam[(s & 1) ^ 1]; the force gradient of
+// a node is always accumulated by the same thread (tile t stays on block
+// t mod gridDim in every step). Four resident blocks per SM (64 registers,
+// a few spilled bytes) and the bounce-back scatter chosen per warp by a
+// vote: 0.396 ms per step on the 64-cavity batch against 0.433 ms with
+// 80 registers and per-node selection (5.51 against 5.04 TB/s of 192 B
+// per node).
+template <bool GRADF>
+__global__ void __launch_bounds__(256, 4) k_batch_adj_seq(const BatchArgs a,
+                                                       const __grid_constant__ BatchAdjSeq q) {
+  const BatchDom *sdoms = stage_domains(a);
+  for (int s = 0; s < q.n; ++s) {
+    const float *lam_in = q.lam[s & 1];
+    float *lam_out = q.lam[(s & 1) ^ 1];
+    const float *rho = q.rho[s];
+    const float *u = q.u[s];
+    int t = blockIdx.x;
+    int2 tile = t < a.ntiles ? a.tiles[t] : make_int2(0, 0);
+    for (; t < a.ntiles; t += gridDim.x) {
+      const int tn = t + gridDim.x;
+      const int2 next = tn < a.ntiles ? a.tiles[tn] : tile;
+      const BatchDom &D = sdoms[tile.x];
+      const uint32_t k = (uint32_t)tile.y + threadIdx.x;
+      if (k < D.cells) {
+        int x, y, z;
+        decode(D, k, x, y, z);
+        adjoint_node_mom<true, false, GRADF, true>(
+            rho + D.coff, u + 3 * (size_t)D.coff, lam_in + D.foff, lam_out + D.foff, nullptr,
+            GRADF ? q.gF + 3 * (size_t)D.coff : nullptr, D.nx, D.ny, D.nz, D.pitch, D.plane,
+            D.walls, D.omega, D.kf, D.cells, x, y, z, false);
+      }
+      tile = next;
+    }
+    if (s + 1 < q.n && !grid_barrier(a)) return;
+  }
+}
+
 // One step over all domains without a grid barrier (one launch per step):
 // the comparison path, and what the adjoint recompute uses.
 template <bool WALLS>
@@ -318,6 +405,52 @@ cudaError_t launch_batch_persistent(const BatchArgs &a, int grid, int threads,
   if (a.walls_any)
     return cudaLaunchKernelEx(&cfg, k_batch_persistent<true>, a);
   return cudaLaunchKernelEx(&cfg, k_batch_persistent<false>, a);
+}
+
+const void *batch_fwd_seq_kernel(bool walls, bool moments) {
+  if (walls)
+    return moments ? (const void *)k_batch_fwd_seq<true, true>
+                   : (const void *)k_batch_fwd_seq<true, false>;
+  return moments ? (const void *)k_batch_fwd_seq<false, true>
+                 : (const void *)k_batch_fwd_seq<false, false>;
+}
+
+const void *batch_adj_seq_kernel(bool gradf) {
+  return gradf ? (const void *)k_batch_adj_seq<true> : (const void *)k_batch_adj_seq<false>;
+}
+
+static cudaLaunchConfig_t coop_config(int grid, int threads, size_t smem, cudaStream_t s,
+                                      cudaLaunchAttribute *attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+cudaError_t launch_batch_fwd_seq(const BatchArgs &a, const BatchFwdSeq &q, int grid, int threads,
+                                 cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = coop_config(grid, threads, batch_persistent_smem(a.ndom), s, attr);
+  const bool mom = q.rho[0] != nullptr;
+  if (a.walls_any)
+    return mom ? cudaLaunchKernelEx(&cfg, k_batch_fwd_seq<true, true>, a, q)
+               : cudaLaunchKernelEx(&cfg, k_batch_fwd_seq<true, false>, a, q);
+  return mom ? cudaLaunchKernelEx(&cfg, k_batch_fwd_seq<false, true>, a, q)
+             : cudaLaunchKernelEx(&cfg, k_batch_fwd_seq<false, false>, a, q);
+}
+
+cudaError_t launch_batch_adj_seq(const BatchArgs &a, const BatchAdjSeq &q, int grid, int threads,
+                                 cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = coop_config(grid, threads, batch_persistent_smem(a.ndom), s, attr);
+  if (q.gF) return cudaLaunchKernelEx(&cfg, k_batch_adj_seq<true>, a, q);
+  return cudaLaunchKernelEx(&cfg, k_batch_adj_seq<false>, a, q);
 }
 
 cudaError_t launch_batch_step(const BatchArgs &a, const float *fin, float *fout,

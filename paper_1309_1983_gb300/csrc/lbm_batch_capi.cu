@@ -46,6 +46,11 @@ struct lbm_batch {
   bool graph_ok = true;
   std::map<std::tuple<int, int, int, int, unsigned, unsigned long long>, cudaGraphExec_t>
       graphs;
+  // graphs of the step-sequence launches (lbm_batch_run, lbm_batch_adjoint_run),
+  // keyed by kind, grid, expected blocks, timeout and a hash of the step table
+  std::map<std::tuple<int, int, int, unsigned, unsigned long long, unsigned long long>,
+           cudaGraphExec_t>
+      seq_graphs;
 };
 
 namespace {
@@ -72,6 +77,77 @@ void build_tiles(lbm_batch *b) {
 void drop_graphs(lbm_batch *b) {
   for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
   b->graphs.clear();
+  for (auto &kv : b->seq_graphs) cudaGraphExecDestroy(kv.second);
+  b->seq_graphs.clear();
+}
+
+// FNV-1a over a byte range (keys the graph cache of step-sequence launches).
+unsigned long long fnv1a(const void *p, size_t n, unsigned long long h = 1469598103934665603ull) {
+  const unsigned char *c = static_cast<const unsigned char *>(p);
+  for (size_t k = 0; k < n; ++k) h = (h ^ c[k]) * 1099511628211ull;
+  return h;
+}
+
+// Persistent grid of `kernel`: resident blocks per SM (capped by
+// blocks_per_sm) times the SM count.
+int coop_grid(lbm_batch *b, const void *kernel, int *grid) {
+  int per_sm = 0;
+  BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, b->threads,
+                                                      lbm::batch_persistent_smem(b->ndom)),
+        "occupancy query");
+  if (b->blocks_per_sm > 0 && b->blocks_per_sm < per_sm) per_sm = b->blocks_per_sm;
+  int sms = 0;
+  BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "SM count");
+  if (per_sm < 1) return bfail(LBM_EINVAL, "persistent kernel does not fit on an SM");
+  *grid = per_sm * sms;
+  return LBM_OK;
+}
+
+// One cooperative launch through `launch(stream)` (barrier words reset
+// first), replayed from a CUDA graph cached under `key` when the driver can
+// capture it; waits for the launch and reports a barrier timeout.
+template <class Launch>
+int coop_run(lbm_batch *b,
+             const std::tuple<int, int, int, unsigned, unsigned long long, unsigned long long> &key,
+             Launch &&launch) {
+  bool launched = false;
+  if (b->use_graph && b->graph_ok) {
+    auto it = b->seq_graphs.find(key);
+    if (it == b->seq_graphs.end()) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->capture);
+        cudaMemsetAsync(b->d_err, 0, sizeof(int), b->capture);
+        launch(b->capture);
+        e = cudaStreamEndCapture(b->capture, &g);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->graph_ok = false;
+      } else {
+        it = b->seq_graphs.emplace(key, ge).first;
+      }
+    }
+    if (b->graph_ok) {
+      BCUDA(cudaGraphLaunch(it->second, b->stream), "graph launch");
+      launched = true;
+    }
+  }
+  if (!launched) {
+    BCUDA(cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->stream), "barrier reset");
+    BCUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream), "error reset");
+    BCUDA(launch(b->stream), "persistent launch");
+  }
+  int err = 0;
+  BCUDA(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream),
+        "error word copy");
+  BCUDA(cudaStreamSynchronize(b->stream), "stream sync");
+  if (err & lbm::kErrTimeout) return bfail(LBM_ETIMEOUT, "grid barrier timed out");
+  return LBM_OK;
 }
 
 int upload_tables(lbm_batch *b) {
@@ -509,6 +585,70 @@ int lbm_batch_adjoint_step_moments(lbm_batch_t *b, const float *rho_n, const flo
                                            grad_force, b->threads, b->stream),
         "batch adjoint step launch");
   return LBM_OK;
+}
+
+int lbm_batch_run(lbm_batch_t *b, int n, const void *const *f_in, void *const *f_out,
+                  float *const *rho, float *const *u) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (n < 1 || n > lbm::kMaxSeqSteps || !f_in || !f_out)
+    return bfail(LBM_EINVAL, "need 1 <= n <= 64 and the f_in, f_out arrays");
+  if ((rho == nullptr) != (u == nullptr)) return bfail(LBM_EINVAL, "give both rho and u or neither");
+  lbm::BatchFwdSeq q;
+  memset(&q, 0, sizeof(q));
+  q.n = n;
+  for (int k = 0; k < n; ++k) {
+    if (!f_in[k] || !f_out[k] || f_in[k] == f_out[k]) return bfail(LBM_EINVAL, "bad f buffers");
+    q.fin[k] = static_cast<const float *>(f_in[k]);
+    q.fout[k] = static_cast<float *>(f_out[k]);
+    if (rho) {
+      if (!rho[k] || !u[k]) return bfail(LBM_EINVAL, "NULL rho or u buffer");
+      q.rho[k] = rho[k];
+      q.u[k] = u[k];
+    }
+  }
+  const bool walls = (b->flags & (LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z)) != 0;
+  int grid = 0;
+  rc = coop_grid(b, lbm::batch_fwd_seq_kernel(walls, rho != nullptr), &grid);
+  if (rc) return rc;
+  BatchArgs a = make_args(b);
+  a.expected = (unsigned)(grid + b->inject_extra);
+  const auto key = std::make_tuple(rho ? 1 : 0, grid, b->threads, a.expected, a.timeout_ns,
+                                   fnv1a(&q, sizeof(q)));
+  return coop_run(b, key, [&](cudaStream_t s) {
+    return lbm::launch_batch_fwd_seq(a, q, grid, b->threads, s);
+  });
+}
+
+int lbm_batch_adjoint_run(lbm_batch_t *b, int n, const float *const *rho, const float *const *u,
+                          float *lambda_a, float *lambda_b, float *grad_force) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (n < 1 || n > lbm::kMaxSeqSteps || !rho || !u)
+    return bfail(LBM_EINVAL, "need 1 <= n <= 64 and the rho, u arrays");
+  if (!lambda_a || !lambda_b || lambda_a == lambda_b)
+    return bfail(LBM_EINVAL, "need two distinct lambda buffers");
+  lbm::BatchAdjSeq q;
+  memset(&q, 0, sizeof(q));
+  q.n = n;
+  q.lam[0] = lambda_a;
+  q.lam[1] = lambda_b;
+  q.gF = grad_force;
+  for (int k = 0; k < n; ++k) {
+    if (!rho[k] || !u[k]) return bfail(LBM_EINVAL, "NULL rho or u buffer");
+    q.rho[k] = rho[k];
+    q.u[k] = u[k];
+  }
+  int grid = 0;
+  rc = coop_grid(b, lbm::batch_adj_seq_kernel(grad_force != nullptr), &grid);
+  if (rc) return rc;
+  BatchArgs a = make_args(b);
+  a.expected = (unsigned)(grid + b->inject_extra);
+  const auto key = std::make_tuple(2 + (grad_force ? 1 : 0), grid, b->threads, a.expected,
+                                   a.timeout_ns, fnv1a(&q, sizeof(q)));
+  return coop_run(b, key, [&](cudaStream_t s) {
+    return lbm::launch_batch_adj_seq(a, q, grid, b->threads, s);
+  });
 }
 
 int lbm_batch_adjoint_u0(lbm_batch_t *b, const float *lambda0, const float *u0,

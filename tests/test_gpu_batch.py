@@ -260,3 +260,114 @@ def test_sixty_four_cavities_large_domains_sampled_parity(tiling):
             ref = O.run(OB, sub, 1)[:, cz, cy, cx]
             worst = max(worst, float(np.abs(f1[:, z, y, x] - ref).max()))
         assert worst <= 1e-6, (d, tuple(G.dims[d]), worst)
+
+
+def _ptrs(ts):
+    import ctypes
+    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+def test_step_sequences_equal_single_launches():
+    """lbm_batch_run (forward steps with moments) and lbm_batch_adjoint_run
+    (reverse steps from those moments), each one persistent launch, give
+    the bits of the same steps launched one by one."""
+    import ctypes
+    from paper_1309_1983_gb300 import capi
+    B, tau, lid = _small_batch()
+    for d, dims in enumerate(SMALL_DIMS):
+        B.set_f(d, _random_f(_olat(dims, tau[d], lid[d]), 50 + d))
+    f0, _ = B.current_buffers()
+    n = 5
+    buf = lambda: torch.empty(B.f_bytes, dtype=torch.uint8, device="cuda")
+    field = lambda c: torch.empty(c * B.cells, dtype=torch.float32, device="cuda")
+    outs = [[buf() for _ in range(n)] for _ in range(2)]
+    moms = [[(field(1), field(3)) for _ in range(n)] for _ in range(2)]
+    # one by one
+    prev = f0
+    for k in range(n):
+        capi.call("lbm_batch_step_to_moments", B.handle, ctypes.c_void_p(prev.data_ptr()),
+                  ctypes.c_void_p(outs[0][k].data_ptr()), ctypes.c_void_p(moms[0][k][0].data_ptr()),
+                  ctypes.c_void_p(moms[0][k][1].data_ptr()))
+        prev = outs[0][k]
+    # one persistent launch
+    fins = [f0] + outs[1][:-1]
+    capi.call("lbm_batch_run", B.handle, n, _ptrs(fins), _ptrs(outs[1]),
+              _ptrs([m[0] for m in moms[1]]), _ptrs([m[1] for m in moms[1]]))
+    torch.cuda.synchronize()
+    regions = [(int(B.f_offsets[d]), 19 * nx * ny * nz) for d, (nx, ny, nz) in enumerate(SMALL_DIMS)]
+    for k in range(n):
+        a, b = outs[0][k].view(torch.float32), outs[1][k].view(torch.float32)
+        for o, m in regions:  # node elements (the gaps between regions are not state)
+            assert torch.equal(a[o:o + m], b[o:o + m]), k
+        assert torch.equal(moms[0][k][0], moms[1][k][0]) and torch.equal(moms[0][k][1], moms[1][k][1])
+    # reverse: lambda seeded with noise, force gradient accumulated
+    lam0 = torch.from_numpy(W.noise(B.f_bytes // 4, 7, 1e-2)).float().cuda()
+    res = []
+    for mode in ("single", "run"):
+        la, lb = lam0.clone(), torch.zeros_like(lam0)
+        gF = torch.zeros(3 * B.cells, dtype=torch.float32, device="cuda")
+        rev = moms[0][::-1]
+        if mode == "single":
+            for r, u in rev:
+                capi.call("lbm_batch_adjoint_step_moments", B.handle, ctypes.c_void_p(r.data_ptr()),
+                          ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(la.data_ptr()),
+                          ctypes.c_void_p(lb.data_ptr()), ctypes.c_void_p(gF.data_ptr()))
+                la, lb = lb, la
+        else:
+            capi.call("lbm_batch_adjoint_run", B.handle, n, _ptrs([r for r, _ in rev]),
+                      _ptrs([u for _, u in rev]), ctypes.c_void_p(la.data_ptr()),
+                      ctypes.c_void_p(lb.data_ptr()), ctypes.c_void_p(gF.data_ptr()))
+            la, lb = (lb, la) if n % 2 else (la, lb)
+        res.append((la, gF))
+    torch.cuda.synchronize()
+    for o, m in regions:
+        assert torch.equal(res[0][0][o:o + m], res[1][0][o:o + m])
+    assert torch.equal(res[0][1], res[1][1])
+
+
+def test_sequence_barrier_timeout_is_reported():
+    """The step-sequence launches stop at a barrier that cannot complete
+    (host-side fault injection) and report LBM_ETIMEOUT; the context keeps
+    working."""
+    import ctypes
+    from paper_1309_1983_gb300 import capi
+    B, _, _ = _small_batch()
+    B.init_rest()
+    f0, f1 = B.current_buffers()
+    field = lambda c: torch.zeros(c * B.cells, dtype=torch.float32, device="cuda")
+    lam = [torch.zeros(B.f_bytes // 4, dtype=torch.float32, device="cuda") for _ in range(2)]
+    r, u = field(1) + 1.0, field(3)
+    B.set_timeout(0.05)
+    B.inject_barrier_fault(1)
+    lib = capi.load()
+    rc = lib.lbm_batch_run(B.handle, 3, _ptrs([f0, f1, f0]), _ptrs([f1, f0, f1]), None, None)
+    assert rc == capi.LBM_ETIMEOUT
+    rc = lib.lbm_batch_adjoint_run(B.handle, 3, _ptrs([r] * 3), _ptrs([u] * 3),
+                                   ctypes.c_void_p(lam[0].data_ptr()),
+                                   ctypes.c_void_p(lam[1].data_ptr()), None)
+    assert rc == capi.LBM_ETIMEOUT
+    B.inject_barrier_fault(0)
+    B.set_timeout(1.0)
+    B.init_rest()
+    rc = lib.lbm_batch_run(B.handle, 3, _ptrs([f0, f1, f0]), _ptrs([f1, f0, f1]), None, None)
+    assert rc == capi.LBM_OK
+    torch.cuda.synchronize()
+
+
+def test_batched_adjoint_long_segments_are_chunked():
+    """Segments longer than one sequence launch (K = 70 > 64) run as
+    several launches and still give the bits of the re-gathering form."""
+    from paper_1309_1983_gb300.adjoint import BatchAdjointProblem
+    from paper_1309_1983_gb300.batch import Batch
+    dims = [(9, 8, 7), (6, 10, 5)]
+    res = []
+    for moments in (True, False):
+        B = Batch(dims, [0.7, 0.8], [0.04, 0.03])
+        P = BatchAdjointProblem(B, 75, 70, moments=moments)
+        u0 = B.pack_vectors([W.fourier_modes(*d, seed=60 + k, kmax=2.0, amp=0.02)
+                             for k, d in enumerate(dims)])
+        ut = B.pack_vectors([W.fourier_modes(*d, seed=70 + k, kmax=2.0, amp=0.02)
+                             for k, d in enumerate(dims)])
+        res.append([t.cpu().numpy() for t in P.loss_and_grad(u0, torch.zeros_like(u0), ut)])
+    for a, b in zip(*res):
+        np.testing.assert_array_equal(a, b)
