@@ -90,8 +90,10 @@ def kernel_source_hash():
 
 
 def ncu_traffic(summary_name):
-    """DRAM bytes per launch from a committed ncu summary, or None when the
-    summary is missing or was taken on a different kernel source."""
+    """DRAM bytes (read + write) per launch of the step kernel, measured by
+    ncu at the benchmark's full size and recorded in a committed summary;
+    None when the summary is missing or was taken on a different kernel
+    source."""
     path = os.path.join(ROOT, "profiles", summary_name)
     try:
         kv = {}
@@ -102,7 +104,7 @@ def ncu_traffic(summary_name):
                     kv[k.strip()] = v.strip()
         if kv.get("kernel_source_sha256_16") != kernel_source_hash():
             return None
-        return float(kv["dram_bytes_per_launch_scaled"])
+        return float(kv["dram_bytes_per_launch"])
     except Exception:
         return None
 
@@ -220,12 +222,14 @@ def run_reference(args):
     sample = (f"FP64 oracle, one update of a periodic {n}^3 shear-wave lattice per step, "
               f"{args.steps} steps in one oracle call (bounded sample of the {args.n}^3 "
               f"workload; same per-node arithmetic)")
+    # the config names the lattice actually timed, and the workload it samples
+    config = dict(workload_config(n), sample_of=workload_config(args.n)["workload"])
     line = {
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.n),
+        "config": config,
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": O.max_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -592,7 +596,7 @@ def run_ours(args):
     peak, peak_kind = measured_hbm()
     achieved = bpl * cells / (step_ms / 1e3) / 1e9
     default_run = n == 384 and args.storage == "f32" and args.geometry == "periodic"
-    traffic = ncu_traffic("k_step_f32_periodic_384.txt") if default_run else None
+    traffic = ncu_traffic("launches_bench_periodic_384.txt") if default_run else None
 
     # end to end through the C ABI on host buffers
     u0_h = torch.from_numpy(W.shear_wave(n, n, n, AMP)).float().pin_memory()
