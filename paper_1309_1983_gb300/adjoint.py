@@ -45,6 +45,7 @@ class _Checkpointed:
         self._segment = []
         self._mom_seg = []
         self._ckpt_pool = []
+        self._tail_moments = False  # the last segment's moments are in _mom_seg
 
     # -- supplied by subclasses ------------------------------------------------
     def _fbuf(self):
@@ -98,12 +99,20 @@ class _Checkpointed:
         return lam_a, lam_b
 
     # -- driver -------------------------------------------------------------------
-    def forward(self, u0, F):
+    def _moment_buffers(self, m):
+        while len(self._mom_seg) < m:
+            self._mom_seg.append(self._mom())
+        return self._mom_seg[:m]
+
+    def forward(self, u0, F, keep_tail=False):
         """f^0 = f^eq(1, u0), then T steps keeping every K-th state.
         Returns (f_T, checkpoints); the buffers stay valid until the next
-        call of forward()."""
+        call of forward(). keep_tail (with moments=True): the last segment's
+        steps also write the rho, u their collisions used, so that the next
+        backward() need not recompute that segment."""
         if self._scratch is None:
             self._scratch = [self._fbuf(), self._fbuf()]
+        self._tail_moments = False
         f0 = self._init(u0, F)
         ckpts = [f0]
         prev = f0
@@ -121,7 +130,11 @@ class _Checkpointed:
             fouts.append(dst)
             prev = dst
             if n % self.K == 0 or n == self.T:  # one segment per call
-                self._run(fins, fouts)
+                if n == self.T and keep_tail and self.moments:
+                    self._run_mom(fins, fouts, self._moment_buffers(len(fins)))
+                    self._tail_moments = True
+                else:
+                    self._run(fins, fouts)
                 fins, fouts = [], []
         return prev, ckpts
 
@@ -132,9 +145,7 @@ class _Checkpointed:
         loss = torch.zeros((), dtype=torch.float64, device=gF.device)
         self._seed(f_T, ut, lam_a, gF, loss)
         if self.moments:
-            need = min(self.K, self.T)
-            while len(self._mom_seg) < need:
-                self._mom_seg.append(self._mom())
+            self._moment_buffers(min(self.K, self.T))
         else:
             need = min(self.K, self.T) - 1
             while len(self._segment) < need:
@@ -145,9 +156,10 @@ class _Checkpointed:
             if self.moments:
                 # f_T (a scratch buffer) is no longer needed after the seed
                 m = stop - start
-                fins = [ckpts[s]] + [self._scratch[k % 2] for k in range(m - 1)]
-                fouts = [self._scratch[k % 2] for k in range(m)]
-                self._run_mom(fins, fouts, self._mom_seg[:m])
+                if not (self._tail_moments and s == len(ckpts) - 1):
+                    fins = [ckpts[s]] + [self._scratch[k % 2] for k in range(m - 1)]
+                    fouts = [self._scratch[k % 2] for k in range(m)]
+                    self._run_mom(fins, fouts, self._mom_seg[:m])
                 lam_a, lam_b = self._reverse(self._mom_seg[:m][::-1], lam_a, lam_b, gF)
                 continue
             states = [ckpts[s]]
@@ -159,13 +171,14 @@ class _Checkpointed:
                 lam_a, lam_b = lam_b, lam_a
         gu0 = self._field()
         self._u0grad(lam_a, u0, gu0)
+        self._tail_moments = False  # the segment buffers now hold the first segment's
         return loss, gu0, gF
 
     def loss_and_grad(self, u0, F, u_target):
         u0 = u0.detach().float().contiguous()
         F = F.detach().float().contiguous()
         ut = u_target.detach().float().contiguous()
-        f_T, ckpts = self.forward(u0, F)
+        f_T, ckpts = self.forward(u0, F, keep_tail=True)
         return self.backward(f_T, ckpts, u0, ut)
 
     def loss(self, u0, F, u_target):
@@ -328,7 +341,7 @@ class VelocityMismatch(torch.autograd.Function):
         u0c = u0.detach().float().contiguous()
         Fc = F.detach().float().contiguous()
         utc = u_target.detach().float().contiguous()
-        f_T, ckpts = problem.forward(u0c, Fc)
+        f_T, ckpts = problem.forward(u0c, Fc, keep_tail=True)
         lam = problem._lam()
         loss = torch.zeros((), dtype=torch.float64, device=u0c.device)
         problem._seed(f_T, utc, lam, None, loss)
