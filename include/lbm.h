@@ -493,9 +493,12 @@ int lbm_batch_adjoint_u0(lbm_batch_t *b, const float *lambda0, const float *u0,
                          float *grad_u0);
 
 /* Step sequences in ONE persistent cooperative launch each (a grid barrier
- * with bounded waits between steps, replayed from a cached CUDA graph), for
- * the checkpointed adjoint's forward segments, segment recompute and
+ * with bounded waits between steps, replayed from a CUDA graph cached per
+ * distinct step table; the handle keeps up to 512 such graphs and drops
+ * them all when a new table would exceed that, or on rebind or retiling),
+ * for the checkpointed adjoint's forward segments, segment recompute and
  * reverse sweeps. Both wait for the launch; LBM_ETIMEOUT as lbm_batch_step.
+ * f and lambda buffers must be 256-byte aligned (LBM_EINVAL otherwise).
  *
  * lbm_batch_run: n in [1, 64] steps; step k reads f_in[k] and writes
  * f_out[k] (device buffers in the batch layout, f_in[k] != f_out[k]; step

@@ -103,6 +103,12 @@ int coop_grid(lbm_batch *b, const void *kernel, int *grid) {
   return LBM_OK;
 }
 
+bool aligned_to(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Graphs kept for step-sequence launches: a checkpointed adjoint uses a few
+// per checkpoint; past this many distinct step tables the cache is emptied.
+constexpr size_t kMaxSeqGraphs = 512;
+
 // One cooperative launch through `launch(stream)` (barrier words reset
 // first), replayed from a CUDA graph cached under `key` when the driver can
 // capture it; waits for the launch and reports a barrier timeout.
@@ -113,6 +119,11 @@ int coop_run(lbm_batch *b,
   bool launched = false;
   if (b->use_graph && b->graph_ok) {
     auto it = b->seq_graphs.find(key);
+    if (it == b->seq_graphs.end() && b->seq_graphs.size() >= kMaxSeqGraphs) {
+      for (auto &kv : b->seq_graphs) cudaGraphExecDestroy(kv.second);
+      b->seq_graphs.clear();
+      it = b->seq_graphs.end();
+    }
     if (it == b->seq_graphs.end()) {
       cudaGraph_t g = nullptr;
       cudaGraphExec_t ge = nullptr;
@@ -599,10 +610,14 @@ int lbm_batch_run(lbm_batch_t *b, int n, const void *const *f_in, void *const *f
   q.n = n;
   for (int k = 0; k < n; ++k) {
     if (!f_in[k] || !f_out[k] || f_in[k] == f_out[k]) return bfail(LBM_EINVAL, "bad f buffers");
+    if (!aligned_to(f_in[k], 256) || !aligned_to(f_out[k], 256))
+      return bfail(LBM_EINVAL, "f buffers must be 256-byte aligned");
     q.fin[k] = static_cast<const float *>(f_in[k]);
     q.fout[k] = static_cast<float *>(f_out[k]);
     if (rho) {
       if (!rho[k] || !u[k]) return bfail(LBM_EINVAL, "NULL rho or u buffer");
+      if (!aligned_to(rho[k], 4) || !aligned_to(u[k], 4))
+        return bfail(LBM_EINVAL, "rho/u misaligned");
       q.rho[k] = rho[k];
       q.u[k] = u[k];
     }
@@ -628,6 +643,9 @@ int lbm_batch_adjoint_run(lbm_batch_t *b, int n, const float *const *rho, const 
     return bfail(LBM_EINVAL, "need 1 <= n <= 64 and the rho, u arrays");
   if (!lambda_a || !lambda_b || lambda_a == lambda_b)
     return bfail(LBM_EINVAL, "need two distinct lambda buffers");
+  if (!aligned_to(lambda_a, 256) || !aligned_to(lambda_b, 256) ||
+      (grad_force && !aligned_to(grad_force, 4)))
+    return bfail(LBM_EINVAL, "lambda buffers must be 256-byte aligned");
   lbm::BatchAdjSeq q;
   memset(&q, 0, sizeof(q));
   q.n = n;
@@ -636,6 +654,8 @@ int lbm_batch_adjoint_run(lbm_batch_t *b, int n, const float *const *rho, const 
   q.gF = grad_force;
   for (int k = 0; k < n; ++k) {
     if (!rho[k] || !u[k]) return bfail(LBM_EINVAL, "NULL rho or u buffer");
+    if (!aligned_to(rho[k], 4) || !aligned_to(u[k], 4))
+      return bfail(LBM_EINVAL, "rho/u misaligned");
     q.rho[k] = rho[k];
     q.u[k] = u[k];
   }

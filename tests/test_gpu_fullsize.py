@@ -102,6 +102,50 @@ def test_cavity_384_sampled_parity():
     assert worst <= ATOL_F, worst
 
 
+def _onsite_axis_block(n, c, walled):
+    """Block indices along one axis for on-site walls (3 nodes wide, so the
+    oracle accepts a walled block), the node's position, and whether the
+    block is walled (only where it holds a lattice wall node)."""
+    if walled and c == 0:
+        return [0, 1, 2], 0, True
+    if walled and c == n - 1:
+        return [n - 3, n - 2, n - 1], 2, True
+    return [(c - 1) % n, c, (c + 1) % n], 1, False
+
+
+def test_onsite_cavity_384_sampled_parity():
+    """On-site walls (the paper's boundary) at the benchmark's size and
+    launch configuration: one step after 20 from rest, sampled nodes
+    (corners, edges, faces, random) against one oracle step on each node's
+    3 x 3 x 3 block (walled where the block holds a lattice wall node, the
+    lid where it holds the lattice's top plane)."""
+    from paper_1309_1983_gb300.lattice import Lattice
+    tau, lid = 0.6, (0.05, 0.0, 0.0)
+    L = Lattice(N, N, N, tau, walls=(True, True, True), lid=lid, onsite=True)
+    L.init_equilibrium()
+    L.step(20)
+    w = O.weights()
+    v = _view(L)
+    samples = _samples(N, np.random.default_rng(3))
+    blocks = []
+    for (x, y, z) in samples:
+        xi, cx, wx = _onsite_axis_block(N, x, True)
+        yi, cy, wy = _onsite_axis_block(N, y, True)
+        zi, cz, wz = _onsite_axis_block(N, z, True)
+        sub = v[:, zi][:, :, yi][:, :, :, xi].double().cpu().numpy() + w[:, None, None, None]
+        OB = O.Lattice(3, 3, 3, tau, walls=(wx, wy, wz), lid=bool(wz and zi[-1] == N - 1),
+                       lid_u=lid, onsite=True)
+        blocks.append((sub, OB, (cx, cy, cz)))
+    L.step(1)
+    v = _view(L)
+    worst = 0.0
+    for (x, y, z), (sub, OB, (cx, cy, cz)) in zip(samples, blocks):
+        ref = O.run(OB, sub, 1)[:, cz, cy, cx]
+        got = v[:, z, y, x].double().cpu().numpy() + w
+        worst = max(worst, float(np.abs(got - ref).max()))
+    assert worst <= ATOL_F, worst
+
+
 def test_mass_conserved_at_full_size():
     """Periodic and closed-cavity lattices conserve mass: after 200 steps at
     384^3 the FP64 total differs from N^3 by rounding only (FP32 values ~1e-3
