@@ -186,6 +186,16 @@ int lbm_set_block(lbm_t *h, int bx, int by);
  * one two-value store per direction (16-bit: two-value conversions);
  * bit-identical results. Block shape: lbm_set_pair_block. */
 #define LBM_KERNEL_X2 4
+/* LBM_KERNEL_X4 (16-bit storage, periodic axes and halfway walls; a
+ * measured alternative, slower than LBM_KERNEL_X2 on GB300): four
+ * x-adjacent nodes per thread; per direction one aligned 4-value load, one
+ * single-value load for the value beyond the group when e_x != 0, two
+ * 2-value stores; walls on x need only that single load to point at the
+ * bounced value, walls on y or z move the whole group load; bit-identical
+ * results. Block shape: lbm_set_pair_block, read as groups of four along x.
+ * With nx not a multiple of 4 the padding elements after a row's last node
+ * up to the next multiple of 4 are loaded and stored (never used). */
+#define LBM_KERNEL_X4 5
 int lbm_set_kernel(lbm_t *h, int variant);
 
 /* How the one-node kernel applies bounce-back: LBM_WALLS_SELECT picks each

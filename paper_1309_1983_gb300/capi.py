@@ -48,6 +48,7 @@ LBM_KERNEL_PAIR = 1
 LBM_KERNEL_BULK = 2
 LBM_KERNEL_BULK1 = 3
 LBM_KERNEL_X2 = 4
+LBM_KERNEL_X4 = 5
 
 
 class LBMError(RuntimeError):

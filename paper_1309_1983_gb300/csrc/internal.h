@@ -55,6 +55,10 @@ cudaError_t launch_step_x2(int storage, bool moments, const StepArgs &a, int bxp
                            cudaStream_t s);
 cudaError_t launch_step_pair16(int storage, bool moments, const StepArgs &a, int bxp, int by,
                                cudaStream_t s);
+// Four x-adjacent nodes per thread (bxq groups of four per block row, `by`
+// rows); periodic axes and halfway walls.
+cudaError_t launch_step_x4(int storage, bool moments, const StepArgs &a, int bxq, int by,
+                           cudaStream_t s);
 // Bulk-copy (TMA) staged step, persistent over tiles; variant 0: 2-row tiles,
 // variant 1: 1-row tiles with a deeper pipeline. err receives kErrTimeout if
 // a bounded mbarrier wait gave up.

@@ -103,7 +103,8 @@ StepArgs make_args(const lbm_t *h, const void *fin, void *fout) {
   for (int k = 0; k < 3; ++k) a.lid[k] = h->lid[k];
   a.wall_select = h->wall_mode == LBM_WALLS_SELECT ||
                   (h->wall_mode == LBM_WALLS_AUTO &&
-                   (h->storage == lbm::kF32 || h->nx < 256 || h->kernel == LBM_KERNEL_X2));
+                   (h->storage == lbm::kF32 || h->nx < 256 || h->kernel == LBM_KERNEL_X2 ||
+                    h->kernel == LBM_KERNEL_X4));
   for (int i = 0; i < lbm::Q; ++i) {
     a.lidc[i] = 0.0f;
     if ((h->flags & LBM_LID) && lbm::kEz[i] == -1)
@@ -153,6 +154,8 @@ cudaError_t launch_one_step(const lbm_t *h, bool mom, const StepArgs &a, cudaStr
     return lbm::launch_step_pair16(h->storage, mom, a, h->pbx, h->pby, s);
   if (h->kernel == LBM_KERNEL_X2)
     return lbm::launch_step_x2(h->storage, mom, a, h->pbx, h->pby, s);
+  if (h->kernel == LBM_KERNEL_X4)
+    return lbm::launch_step_x4(h->storage, mom, a, h->pbx, h->pby, s);
   if ((h->kernel == LBM_KERNEL_BULK || h->kernel == LBM_KERNEL_BULK1) && !mom)
     return lbm::launch_step_bulk(h->storage, a, h->scr.err,
                                  h->kernel == LBM_KERNEL_BULK1 ? 1 : 0, h->sms, s);
@@ -474,10 +477,12 @@ int lbm_set_block(lbm_t *h, int bx, int by) {
 int lbm_set_kernel(lbm_t *h, int variant) {
   if (!h) return fail(LBM_EINVAL, "NULL handle");
   if (variant != LBM_KERNEL_NODE && variant != LBM_KERNEL_PAIR && variant != LBM_KERNEL_BULK &&
-      variant != LBM_KERNEL_BULK1 && variant != LBM_KERNEL_X2)
+      variant != LBM_KERNEL_BULK1 && variant != LBM_KERNEL_X2 && variant != LBM_KERNEL_X4)
     return fail(LBM_EINVAL, "unknown kernel variant");
   if (variant == LBM_KERNEL_PAIR && h->storage == lbm::kF32)
     return fail(LBM_EINVAL, "the shuffle pair kernel needs 16-bit storage");
+  if (variant == LBM_KERNEL_X4 && h->storage == lbm::kF32)
+    return fail(LBM_EINVAL, "the four-node kernel needs 16-bit storage");
   if (onsite(h) && variant != LBM_KERNEL_X2 && variant != LBM_KERNEL_NODE)
     return fail(LBM_EINVAL, "on-site walls run on LBM_KERNEL_X2 or LBM_KERNEL_NODE");
   h->kernel = variant;

@@ -26,57 +26,10 @@
 #include "d3q19.cuh"
 #include "internal.h"
 #include "onsite.cuh"
+#include "pack.cuh"
 #include "stream.cuh"
 
 namespace lbm {
-
-// Loads and stores of an aligned pair of values, as two floats.
-template <int S>
-struct Pack16;
-
-template <>
-struct Pack16<0> {
-  static __device__ __forceinline__ float2 load(const float *p) {
-    return __ldg(reinterpret_cast<const float2 *>(p));
-  }
-  static __device__ __forceinline__ void store(float *p, float lo, float hi) {
-    __stcs(reinterpret_cast<float2 *>(p), make_float2(lo, hi));
-  }
-};
-
-template <>
-struct Pack16<1> {
-  static __device__ __forceinline__ float2 load(const __half *p) {
-    return unpack(__ldg(reinterpret_cast<const unsigned int *>(p)));
-  }
-  static __device__ __forceinline__ void store(__half *p, float lo, float hi) {
-    __stcs(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
-  }
-  static __device__ __forceinline__ float2 unpack(uint32_t v) {
-    return __half22float2(*reinterpret_cast<const __half2 *>(&v));
-  }
-  static __device__ __forceinline__ uint32_t pack(float lo, float hi) {
-    const __half2 h = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&h);
-  }
-};
-
-template <>
-struct Pack16<2> {
-  static __device__ __forceinline__ float2 load(const __nv_bfloat16 *p) {
-    return unpack(__ldg(reinterpret_cast<const unsigned int *>(p)));
-  }
-  static __device__ __forceinline__ void store(__nv_bfloat16 *p, float lo, float hi) {
-    __stcs(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
-  }
-  static __device__ __forceinline__ float2 unpack(uint32_t v) {
-    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v));
-  }
-  static __device__ __forceinline__ uint32_t pack(float lo, float hi) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&h);
-  }
-};
 
 // Pulled values of both nodes for direction i (bounce-back by address
 // selection when SEL; the e_x = 0 pulls of the pair share y, z, hence their

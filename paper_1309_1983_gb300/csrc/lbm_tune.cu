@@ -84,7 +84,8 @@ int lbm_autotune(lbm_t *h, const char *cache_path, int steps, int *bx_out, int *
   if (!h) return lbm::set_error(LBM_EINVAL, "NULL handle");
   if (!h->bound) return lbm::set_error(LBM_EUNBOUND, "handle not bound");
   if (steps < 1 || steps > 100000) return lbm::set_error(LBM_EINVAL, "steps in [1, 100000]");
-  const bool pair = h->kernel == LBM_KERNEL_PAIR || h->kernel == LBM_KERNEL_X2;
+  const bool pair =
+      h->kernel == LBM_KERNEL_PAIR || h->kernel == LBM_KERNEL_X2 || h->kernel == LBM_KERNEL_X4;
   char geo[160];
   std::snprintf(geo, sizeof geo, "lattice/%dx%dx%d/flags%u/kernel%d/walls%d", h->nx, h->ny,
                 h->nz, h->flags, h->kernel, h->wall_mode);

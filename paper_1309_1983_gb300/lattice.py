@@ -118,12 +118,13 @@ class Lattice:
         capi.call("lbm_set_block", self._h, int(bx), int(by))
 
     def set_kernel(self, variant):
-        """"node" (one node per thread), "pair" / "x2" (16-bit storage only,
-        two nodes per thread), or "bulk" / "bulk1" (rows staged in shared
-        memory by bulk copies)."""
+        """"node" (one node per thread), "x2" (two nodes per thread, the
+        default), "x4" (four nodes per thread), "pair" (16-bit storage
+        only, two nodes per thread with warp shuffles), or "bulk" / "bulk1"
+        (rows staged in shared memory by bulk copies)."""
         v = {"node": capi.LBM_KERNEL_NODE, "pair": capi.LBM_KERNEL_PAIR,
              "bulk": capi.LBM_KERNEL_BULK, "bulk1": capi.LBM_KERNEL_BULK1,
-             "x2": capi.LBM_KERNEL_X2}[variant]
+             "x2": capi.LBM_KERNEL_X2, "x4": capi.LBM_KERNEL_X4}[variant]
         capi.call("lbm_set_kernel", self._h, v)
 
     def set_graph_steps(self, steps):

@@ -6,7 +6,7 @@ at a few GB of device memory so that a full ``ncu`` capture, which saves and
 restores device memory around its passes, ends in about a minute.
 
     python -m paper_1309_1983_gb300.profile_cases step --geometry cavity --storage f16 --n 256
-        init + 4 plain step launches (k_step_x2 by default)
+        init + 4 plain step launches (k_step_x2 by default; --kernel x4 / node)
     python -m paper_1309_1983_gb300.profile_cases batch-adjoint --steps 4
         the 64-cavity batch: one forward sequence with moments, then two
         reverse-sequence launches (k_batch_adj_seq) of `steps` steps each
@@ -20,13 +20,14 @@ import sys
 
 
 def step(geometry: str = "cavity", storage: str = "f16", n: int = 256, launches: int = 4,
-         tau: float = 0.55) -> None:
+         tau: float = 0.55, kernel: str = "x2") -> None:
     import torch
     from .lattice import Lattice
     walls = (geometry == "cavity",) * 3
     L = Lattice(n, n, n, tau, walls=walls, lid=(0.05, 0.0, 0.0) if geometry == "cavity" else None,
                 storage=storage)
     L.set_graph_steps(0)
+    L.set_kernel(kernel)
     L.init_equilibrium()
     for _ in range(launches):
         L.step(1)
@@ -71,12 +72,13 @@ def main(argv=None) -> int:
     s.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16"])
     s.add_argument("--n", type=int, default=256)
     s.add_argument("--launches", type=int, default=4)
+    s.add_argument("--kernel", default="x2", choices=["x2", "x4", "node"])
     b = sub.add_parser("batch-adjoint")
     b.add_argument("--steps", type=int, default=4)
     b.add_argument("--launches", type=int, default=2)
     a = p.parse_args(argv)
     if a.case == "step":
-        step(a.geometry, a.storage, a.n, a.launches)
+        step(a.geometry, a.storage, a.n, a.launches, kernel=a.kernel)
     else:
         batch_adjoint(a.steps, a.launches)
     print("ok")

@@ -9,9 +9,11 @@ filled with the byte 0xFF, a NaN in FP32, FP16 and BF16 alike. States are set
 by initialisation kernels that write node elements only; after each group
 of kernels every byte outside the node elements must still be 0xFF.
 
-The one documented exception: the two-node step kernels (LBM_KERNEL_X2, the
+The documented exceptions: the two-node step kernels (LBM_KERNEL_X2, the
 default, and LBM_KERNEL_PAIR) load and store the padding element that
-follows the last node of an odd-length row, together with that node.
+follows the last node of an odd-length row, together with that node, and
+the four-node kernel (LBM_KERNEL_X4) the padding elements up to the next
+multiple of four.
 """
 
 import ctypes
@@ -47,12 +49,15 @@ def _guard_intact(full, nbytes):
     return bool((full[nbytes:] == 0xFF).all())
 
 
-def _f_outside_intact(full, nbytes, elem_bytes, pitch, nx, ny, nz, pad_written=False):
-    """Guard and row padding of an f-layout buffer [19][nz][ny][pitch]."""
+def _f_outside_intact(full, nbytes, elem_bytes, pitch, nx, ny, nz, pad_written=False,
+                      group=2):
+    """Guard and row padding of an f-layout buffer [19][nz][ny][pitch];
+    with pad_written, the padding up to the next multiple of `group` nodes
+    (the multi-node kernels' last group) may have been written."""
     if not _guard_intact(full, nbytes):
         return "guard"
     v = full[:nbytes].view(19, nz, ny, pitch * elem_bytes)
-    first = nx + (1 if pad_written and nx % 2 == 1 else 0)
+    first = -(-nx // group) * group if pad_written else nx
     pad = v[..., first * elem_bytes:]
     if pad.numel() and not bool((pad == 0xFF).all()):
         return "row padding"
@@ -89,10 +94,12 @@ def test_forward_kernels_write_only_node_elements(storage, geom, shape):
     L._bind()
     h = L.handle
 
+    group = [2]
+
     def check(tag, pad_written):
         torch.cuda.synchronize()
         for name, full in (("A", A), ("B", B)):
-            bad = _f_outside_intact(full, fb, eb, pitch, nx, ny, nz, pad_written)
+            bad = _f_outside_intact(full, fb, eb, pitch, nx, ny, nz, pad_written, group[0])
             assert bad is None, (tag, name, bad)
 
     u0 = torch.from_numpy(W.noise((3, nz, ny, nx), 1, 0.03)).float().cuda()
@@ -100,9 +107,11 @@ def test_forward_kernels_write_only_node_elements(storage, geom, shape):
     check("init", False)
     L.step(3)  # default two-node kernel
     check("x2", True)
-    kernels = ["node", "bulk", "bulk1"] + (["pair"] if storage != "f32" else [])
+    kernels = ["node", "bulk", "bulk1"] + (["pair", "x4"] if storage != "f32" else [])
     for k in kernels:
         L.set_kernel(k)
+        if k == "x4":
+            group[0] = 4
         L.step(2)
         check(k, True)
     L.set_kernel("x2")

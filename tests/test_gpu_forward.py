@@ -419,3 +419,33 @@ def test_two_node_kernel_is_bit_identical_fp32(geom, shape, force, mode):
         outs.append((L.get_f(), rho.cpu(), u.cpu()))
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
     assert torch.equal(outs[0][1], outs[1][1]) and torch.equal(outs[0][2], outs[1][2])
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("geom", sorted(GEOMS))
+@pytest.mark.parametrize("shape", [(37, 11, 9), (64, 5, 3), (1, 7, 6), (6, 4, 5), (130, 3, 2),
+                                   (3, 2, 4), (384, 2, 3)],
+                         ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("force", [False, True])
+def test_four_node_kernel_is_bit_identical(storage, geom, shape, force):
+    """The four-node kernel (16-bit storage) computes the one-node kernel's
+    bits on every geometry: rows whose length is not a multiple of 4
+    (padding nodes in the last group), rows of 1 to 3 nodes (x = 0 and
+    x = nx - 1 in the same group), a body force and the fused moments."""
+    nx, ny, nz = shape
+    g = GEOMS[geom]
+    OL = _olat(nx, ny, nz, 0.6)
+    f0 = _random_state(OL, 18)
+    F = torch.from_numpy(W.noise((3,) + OL.shape, 19, 1e-3)).float()
+    outs = []
+    for kern in ("node", "x4"):
+        L = _lat(nx, ny, nz, 0.6, g["walls"], g["lid"], storage=storage, force=force)
+        L.set_kernel(kern)
+        if force:
+            L.force.copy_(F)
+        L.set_f(f0)
+        L.step(3)
+        rho, u = L.step_moments(2)
+        outs.append((L.get_f(), rho.cpu(), u.cpu()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    assert torch.equal(outs[0][1], outs[1][1]) and torch.equal(outs[0][2], outs[1][2])
