@@ -256,13 +256,19 @@ def timed_steps(L, steps, torch):
 
 def extra_workloads(torch, n, steps=100, warmup=10):
     """Secondary workloads of the same hot path, each timed like the main
-    one: the paper's lid-driven cavity (FP32) and 16-bit storage."""
+    one: the paper's lid-driven cavity (FP32 and 16-bit storage; halfway
+    walls, and the on-site walls the paper used, at tau = 0.6 where they
+    are stable)."""
     from paper_1309_1983_gb300.lattice import Lattice
     from paper_1309_1983_gb300 import perfmodel as PM
     out = {}
-    for name, storage, tau in (("cavity_f32", "f32", 0.55), ("cavity_f16", "f16", 0.55),
-                               ("cavity_bf16", "bf16", 0.55)):
-        L = Lattice(n, n, n, tau, walls=(True, True, True), lid=(0.05, 0.0, 0.0), storage=storage)
+    for name, storage, tau, onsite in (("cavity_f32", "f32", 0.55, False),
+                                       ("cavity_f16", "f16", 0.55, False),
+                                       ("cavity_bf16", "bf16", 0.55, False),
+                                       ("cavity_onsite_f32", "f32", 0.6, True),
+                                       ("cavity_onsite_f16", "f16", 0.6, True)):
+        L = Lattice(n, n, n, tau, walls=(True, True, True), lid=(0.05, 0.0, 0.0), storage=storage,
+                    onsite=onsite)
         L.init_equilibrium()
         L.step(warmup)
         ms, per = timed_steps(L, steps, torch)
