@@ -67,6 +67,7 @@ extern "C" {
 #define LBM_ENONFINITE (-5) /* a non-finite density was detected */
 #define LBM_EUNBOUND (-6)   /* no buffers bound to the handle yet */
 #define LBM_ERANGE (-7)     /* size above a documented maximum */
+#define LBM_ENOTSUP (-8)    /* not in this build (the LBM_CHECK calls) */
 
 /* ---- lbm_create flags ---- */
 #define LBM_WALL_X 0x01u     /* bounce-back walls on both x faces */
@@ -536,6 +537,36 @@ int lbm_batch_moments(lbm_batch_t *b, float *rho, float *u);
  * (w_i added back). Synchronous. */
 int lbm_batch_get_f(lbm_batch_t *b, int dom, double *host_f);
 int lbm_batch_set_f(lbm_batch_t *b, int dom, const double *host_f);
+
+/* ---- the LBM_CHECK debug build (a stand-in for a device memory checker) ----
+ * liblbm_check.so is built from the same sources with -DLBM_CHECK
+ * (paper_1309_1983_gb300/build.py: build(check=True)). In it, every load,
+ * store and atomic that a kernel makes on global memory is first tested
+ * against the table of buffers its launch was given (each buffer a call
+ * receives or owns, with the extent and the read / write use documented
+ * above) and against the natural alignment of the access. An access that
+ * fails is NOT performed (a load reads 0, a store is dropped); it is counted
+ * and the first one is kept. Nothing traps and nothing hangs; a refused bulk
+ * copy of the shared-memory kernel (LBM_KERNEL_BULK*) ends in LBM_ETIMEOUT
+ * through its bounded wait. Tables belong to a translation unit, not to a
+ * stream: in a check build, run the calls of one stream at a time. The
+ * normal liblbm.so returns LBM_ENOTSUP from these three calls.
+ *
+ * lbm_check_status: waits for the device, then *refused = accesses refused
+ * since the last reset and *first_addr, *first_bytes, *first_kind (1 read,
+ * 2 write, 3 read-modify-write) the first of them (zeros if none). Any
+ * pointer may be NULL.
+ * lbm_check_reset: waits for the device and zeroes the record.
+ * lbm_check_narrow: every table built from now on ends each range `bytes`
+ * before the end of the buffer it describes (0: exact extents again), so
+ * that the kernels' accesses to the last `bytes` of every buffer are refused
+ * (and not made): a way to see refusals detected and reported while every
+ * access that is made stays inside its buffer. Launches replayed from CUDA
+ * graphs captured earlier keep the tables they were captured with. */
+int lbm_check_status(unsigned long long *refused, unsigned long long *first_addr,
+                     unsigned int *first_bytes, unsigned int *first_kind);
+int lbm_check_reset(void);
+int lbm_check_narrow(size_t bytes);
 
 #ifdef __cplusplus
 }

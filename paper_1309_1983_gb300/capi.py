@@ -4,6 +4,8 @@ Argument marshalling only: every function here forwards to the C entry
 point of the same name and raises :class:`LBMError` on a non-zero status.
 Nothing computes on the host. Loading fails loudly if the library has not
 been built (``python -m paper_1309_1983_gb300.build``); there is no fallback.
+``LBM_LIBRARY`` (environment) names another build of the same library to
+load instead, e.g. the checked debug build ``liblbm_check.so``.
 """
 
 from __future__ import annotations
@@ -13,7 +15,7 @@ import os
 import re
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "liblbm.so")
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_PKG, "liblbm.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "lbm.h")
 
 LBM_OK = 0
@@ -24,6 +26,7 @@ LBM_ETIMEOUT = -4
 LBM_ENONFINITE = -5
 LBM_EUNBOUND = -6
 LBM_ERANGE = -7
+LBM_ENOTSUP = -8
 
 LBM_WALL_X = 0x01
 LBM_WALL_Y = 0x02
@@ -134,6 +137,9 @@ _SIGNATURES = {
     "lbm_batch_adjoint_u0": [_vp, _vp, _vp, _vp],
     "lbm_batch_run": [_vp, _i, _vp, _vp, _vp, _vp],
     "lbm_batch_adjoint_run": [_vp, _i, _vp, _vp, _vp, _vp, _vp],
+    "lbm_check_status": [_vp, _vp, _vp, _vp],
+    "lbm_check_reset": [],
+    "lbm_check_narrow": [ctypes.c_size_t],
 }
 _RESTYPE = {"lbm_strerror": ctypes.c_char_p, "lbm_last_error": ctypes.c_char_p}
 
@@ -154,7 +160,7 @@ def load(path: str = LIB_PATH):
         return _lib
     if not os.path.exists(path):
         raise RuntimeError(
-            f"liblbm.so not found at {path}: build it with "
+            f"library not found at {path}: build it with "
             "`python -m paper_1309_1983_gb300.build` (there is no CPU fallback)")
     lib = ctypes.CDLL(path)
     for name, args in _SIGNATURES.items():
@@ -208,3 +214,12 @@ def moments(h, rho_ptr, u_ptr, want_mass: bool):
     m = ctypes.c_double()
     call("lbm_moments", h, rho_ptr, u_ptr, ctypes.byref(m) if want_mass else None)
     return m.value if want_mass else None
+
+
+def check_status():
+    """The LBM_CHECK build's record: (refused, first_addr, first_bytes,
+    first_kind); raises LBMError(LBM_ENOTSUP) in the normal build."""
+    n, a = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+    b, k = ctypes.c_uint(), ctypes.c_uint()
+    call("lbm_check_status", ctypes.byref(n), ctypes.byref(a), ctypes.byref(b), ctypes.byref(k))
+    return n.value, a.value, b.value, k.value

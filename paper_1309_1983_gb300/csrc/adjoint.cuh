@@ -82,8 +82,8 @@ __device__ __forceinline__ void load_lambda(const float *__restrict__ lam_in, ui
                                             const NodeIdx &n, float (&lam)[Q]) {
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    lam[i] = L2ONLY ? __ldcg(lam_in + (size_t)i * plane + n.c)
-                    : __ldg(lam_in + (size_t)i * plane + n.c);
+    lam[i] = L2ONLY ? LBM_LDCG(lam_in + (size_t)i * plane + n.c)
+                    : LBM_LDG(lam_in + (size_t)i * plane + n.c);
   });
 }
 
@@ -125,9 +125,9 @@ __device__ __forceinline__ void adjoint_core(
   const float keep = 1.0f - om;
 
   if constexpr (GRADF) {
-    gF[dc] += fmaf(kf, sx, 0.5f * Bx);
-    gF[cells + dc] += fmaf(kf, sy, 0.5f * By);
-    gF[2 * (size_t)cells + dc] += fmaf(kf, sz, 0.5f * Bz);
+    LBM_ACC(&gF[dc], fmaf(kf, sx, 0.5f * Bx));
+    LBM_ACC(&gF[cells + dc], fmaf(kf, sy, 0.5f * By));
+    LBM_ACC(&gF[2 * (size_t)cells + dc], fmaf(kf, sz, 0.5f * Bz));
   }
 
   // mu_j = (1 - omega) lambda_j + A + B . e_j, in place, then scattered by P^T
@@ -141,12 +141,12 @@ __device__ __forceinline__ void adjoint_core(
       constexpr int i = decltype(I)::value;
       const size_t idx = bounces<i>(n) ? (size_t)kOpp_v<i> * plane + n.c
                                        : (size_t)i * plane + source_of<i>(n);
-      lam_out[idx] = lam[i];
+      LBM_ST(&lam_out[idx], lam[i]);
     });
   } else {
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      lam_out[(size_t)i * plane + source_of<i>(n)] = lam[i];
+      LBM_ST(&lam_out[(size_t)i * plane + source_of<i>(n)], lam[i]);
     });
   }
 }
@@ -180,9 +180,9 @@ __device__ __forceinline__ void adjoint_node(
   const uint32_t dc = ((uint32_t)z * ny + y) * nx + x;
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
   if constexpr (FORCE) {
-    Fx = __ldg(force + dc);
-    Fy = __ldg(force + cells + dc);
-    Fz = __ldg(force + 2 * (size_t)cells + dc);
+    Fx = LBM_LDG(force + dc);
+    Fy = LBM_LDG(force + cells + dc);
+    Fz = LBM_LDG(force + 2 * (size_t)cells + dc);
   }
   // the same FP32 arithmetic as the forward collision, so rho and u are
   // bit-identical to the ones lbm_step_moments stores
@@ -212,14 +212,14 @@ __device__ __forceinline__ void adjoint_node_mom(
   const uint32_t dc = ((uint32_t)z * ny + y) * nx + x;
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
   if constexpr (FORCE) {
-    Fx = __ldg(force + dc);
-    Fy = __ldg(force + cells + dc);
-    Fz = __ldg(force + 2 * (size_t)cells + dc);
+    Fx = LBM_LDG(force + dc);
+    Fy = LBM_LDG(force + cells + dc);
+    Fz = LBM_LDG(force + 2 * (size_t)cells + dc);
   }
-  const float rho = __ldg(rho_n + dc);
-  const float ux = __ldg(u_n + dc);
-  const float uy = __ldg(u_n + cells + dc);
-  const float uz = __ldg(u_n + 2 * (size_t)cells + dc);
+  const float rho = LBM_LDG(rho_n + dc);
+  const float ux = LBM_LDG(u_n + dc);
+  const float uy = LBM_LDG(u_n + cells + dc);
+  const float uz = LBM_LDG(u_n + 2 * (size_t)cells + dc);
   float lam[Q];
   load_lambda<L2ONLY>(lam_in, plane, n, lam);
   adjoint_core<FORCE, GRADF>(lam, lam_out, gF, plane, n, sel, dc, cells, rho, ux, uy, uz, Fx,
@@ -242,34 +242,34 @@ __device__ __forceinline__ double seed_node(const float *__restrict__ f,
   float d[Q];
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    d[i] = __ldg(f + (size_t)i * plane + c);
+    d[i] = LBM_LDG(f + (size_t)i * plane + c);
   });
   float dr, jx, jy, jz;
   shifted_moments(d, dr, jx, jy, jz);
   const float rho = 1.0f + dr, rinv = __frcp_rn(rho);
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
   if constexpr (FORCE) {
-    Fx = __ldg(force + dc);
-    Fy = __ldg(force + cells + dc);
-    Fz = __ldg(force + 2 * (size_t)cells + dc);
+    Fx = LBM_LDG(force + dc);
+    Fy = LBM_LDG(force + cells + dc);
+    Fz = LBM_LDG(force + 2 * (size_t)cells + dc);
   }
   const float ux = fmaf(-0.5f, Fx, jx) * rinv;
   const float uy = fmaf(-0.5f, Fy, jy) * rinv;
   const float uz = fmaf(-0.5f, Fz, jz) * rinv;
-  const float ex = ux - __ldg(ut + dc);
-  const float ey = uy - __ldg(ut + cells + dc);
-  const float ez = uz - __ldg(ut + 2 * (size_t)cells + dc);
+  const float ex = ux - LBM_LDG(ut + dc);
+  const float ey = uy - LBM_LDG(ut + cells + dc);
+  const float ez = uz - LBM_LDG(ut + 2 * (size_t)cells + dc);
   const float du = fmaf(ex, ux, fmaf(ey, uy, ez * uz));
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr float cx = (float)kEx[i], cy = (float)kEy[i], cz = (float)kEz[i];
-    lam[(size_t)i * plane + c] = ((cx * ex + cy * ey + cz * ez) - du) * rinv;
+    LBM_ST(&lam[(size_t)i * plane + c], ((cx * ex + cy * ey + cz * ez) - du) * rinv);
   });
   if (gF) {
     const float h = -0.5f * rinv;
-    gF[dc] = h * ex;
-    gF[cells + dc] = h * ey;
-    gF[2 * (size_t)cells + dc] = h * ez;
+    LBM_ST(&gF[dc], h * ex);
+    LBM_ST(&gF[cells + dc], h * ey);
+    LBM_ST(&gF[2 * (size_t)cells + dc], h * ez);
   }
   return 0.5 * ((double)ex * ex + (double)ey * ey + (double)ez * ez);
 }
@@ -285,20 +285,20 @@ __device__ __forceinline__ void u0grad_node(const float *__restrict__ lam0,
   float lam[Q];
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    lam[i] = __ldg(lam0 + (size_t)i * plane + c);
+    lam[i] = LBM_LDG(lam0 + (size_t)i * plane + c);
   });
   float ux = 0.f, uy = 0.f, uz = 0.f;
   if (u0) {
-    ux = u0[dc];
-    uy = u0[cells + dc];
-    uz = u0[2 * (size_t)cells + dc];
+    ux = LBM_LD(&u0[dc]);
+    uy = LBM_LD(&u0[cells + dc]);
+    uz = LBM_LD(&u0[2 * (size_t)cells + dc]);
   }
   const LamMoments m = lambda_moments(lam);
   float Lux, Luy, Luz;
   mat_vec(m.L2, ux, uy, uz, Lux, Luy, Luz);
-  grad[dc] = 3.0f * m.L1[0] + 9.0f * Lux - 3.0f * ux * m.L0;
-  grad[cells + dc] = 3.0f * m.L1[1] + 9.0f * Luy - 3.0f * uy * m.L0;
-  grad[2 * (size_t)cells + dc] = 3.0f * m.L1[2] + 9.0f * Luz - 3.0f * uz * m.L0;
+  LBM_ST(&grad[dc], 3.0f * m.L1[0] + 9.0f * Lux - 3.0f * ux * m.L0);
+  LBM_ST(&grad[cells + dc], 3.0f * m.L1[1] + 9.0f * Luy - 3.0f * uy * m.L0);
+  LBM_ST(&grad[2 * (size_t)cells + dc], 3.0f * m.L1[2] + 9.0f * Luz - 3.0f * uz * m.L0);
 }
 
 // FP64 block sum of one value per thread; thread 0 writes it to *out.
@@ -312,7 +312,7 @@ __device__ __forceinline__ void block_sum_to(double acc, double *out) {
   if (wid == 0) {
     acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) *out = acc;
+    if (lane == 0) LBM_ST(out, acc);
   }
 }
 

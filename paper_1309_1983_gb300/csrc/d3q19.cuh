@@ -17,6 +17,8 @@
 
 #include <type_traits>
 
+#include "check.cuh"
+
 namespace lbm {
 
 constexpr int Q = 19;
@@ -56,37 +58,37 @@ struct Store;
 template <>
 struct Store<0> {
   using T = float;
-  static __device__ __forceinline__ float ld(const T *p) { return __ldg(p); }
-  static __device__ __forceinline__ float ld_l2(const T *p) { return __ldcg(p); }
+  static __device__ __forceinline__ float ld(const T *p) { return LBM_LDG(p); }
+  static __device__ __forceinline__ float ld_l2(const T *p) { return LBM_LDCG(p); }
   static __device__ __forceinline__ float ld_smem(const T *p) { return *p; }
-  static __device__ __forceinline__ void st(T *p, float v) { __stcs(p, v); }
+  static __device__ __forceinline__ void st(T *p, float v) { LBM_STCS(p, v); }
 };
 template <>
 struct Store<1> {
   using T = __half;
   static __device__ __forceinline__ float ld(const T *p) {
-    return __half2float(__ldg(p));
+    return __half2float(LBM_LDG(p));
   }
   static __device__ __forceinline__ float ld_l2(const T *p) {
-    return __half2float(__ldcg(p));
+    return __half2float(LBM_LDCG(p));
   }
   static __device__ __forceinline__ float ld_smem(const T *p) { return __half2float(*p); }
   static __device__ __forceinline__ void st(T *p, float v) {
-    __stcs(p, __float2half_rn(v));
+    LBM_STCS(p, __float2half_rn(v));
   }
 };
 template <>
 struct Store<2> {
   using T = __nv_bfloat16;
   static __device__ __forceinline__ float ld(const T *p) {
-    return __bfloat162float(__ldg(p));
+    return __bfloat162float(LBM_LDG(p));
   }
   static __device__ __forceinline__ float ld_l2(const T *p) {
-    return __bfloat162float(__ldcg(p));
+    return __bfloat162float(LBM_LDCG(p));
   }
   static __device__ __forceinline__ float ld_smem(const T *p) { return __bfloat162float(*p); }
   static __device__ __forceinline__ void st(T *p, float v) {
-    __stcs(p, __float2bfloat16_rn(v));
+    LBM_STCS(p, __float2bfloat16_rn(v));
   }
 };
 

@@ -6,6 +6,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "check.cuh"
 #include "lbm.h"
 
 namespace lbm {
@@ -30,6 +31,17 @@ struct StepArgs {
   float lid[3];        // lid velocity u_w
 };
 
+// Buffers of a launch over StepArgs, for the LBM_CHECK tables (check.cuh;
+// not evaluated in the normal build): f in (read) and f out (write) of
+// `elem` bytes per value, the force field (read), the moment outputs
+// (write). 19 directions per node.
+#define LBM_STEP_RANGES(a, elem)                                          \
+  ::lbm::chk_r((a).fin, 19 * (size_t)(a).plane * (elem)),                 \
+      ::lbm::chk_w((a).fout, 19 * (size_t)(a).plane * (elem)),            \
+      ::lbm::chk_r((a).force, 3 * (size_t)(a).cells * sizeof(float)),     \
+      ::lbm::chk_w((a).rho, (size_t)(a).cells * sizeof(float)),           \
+      ::lbm::chk_w((a).u, 3 * (size_t)(a).cells * sizeof(float))
+
 struct Scratch {
   double *partials = nullptr;  // per-block FP64 partial sums
   double *sum = nullptr;       // final FP64 reduction result
@@ -44,6 +56,7 @@ enum : int { kErrNonFinite = 1, kErrTimeout = 2 };
 
 // storage codes
 enum : int { kF32 = 0, kF16 = 1, kBF16 = 2 };
+constexpr int elem_bytes_of(int storage) { return storage == kF32 ? 4 : 2; }
 
 cudaError_t launch_step(int storage, bool moments, const StepArgs &a, int bx,
                         int by, cudaStream_t s);
@@ -140,7 +153,22 @@ struct BatchArgs {
   int *err;
   unsigned expected;  // blocks that must reach each grid barrier
   unsigned long long timeout_ns;
+#ifdef LBM_CHECK
+  uint64_t f_elems;   // FP32 values per f (or lambda) buffer of the batch
+  uint32_t cells;     // dense nodes of all domains (field buffers: 1 or 3 per node)
+#endif
 };
+
+// Buffers of a batched launch for the LBM_CHECK tables: the domain and tile
+// tables (read), the barrier words and the error word (read-write); the f
+// buffers are listed by each launcher with the permission it needs.
+#define LBM_BATCH_RANGES(a)                                                  \
+  ::lbm::chk_r((a).doms, (size_t)(a).ndom * sizeof(::lbm::BatchDom)),        \
+      ::lbm::chk_r((a).tiles, (size_t)(a).ntiles * sizeof(int2)),            \
+      ::lbm::chk_rw((a).bar_count, sizeof(unsigned)),                        \
+      ::lbm::chk_rw((a).bar_gen, sizeof(unsigned)), ::lbm::chk_rw((a).err, sizeof(int))
+#define LBM_BATCH_F(a) ((size_t)(a).f_elems * sizeof(float))
+#define LBM_BATCH_FIELD(a, comps) ((size_t)(a).cells * (comps) * sizeof(float))
 
 // Relaxation rate omega passed to every kernel for a relaxation time tau:
 // the FP32 value within 2^-22 (relative) of 1/tau for which omega * (1/12)

@@ -16,6 +16,15 @@ struct AdjArgs {
   double *partials;       // seed only: per-block FP64 loss partials
 };
 
+// Extents for the LBM_CHECK tables: an FP32 state or lambda buffer (19
+// values per node of the pitched layout), and a dense [3][cells] field.
+static inline size_t adj_lambda_bytes(const StepArgs &g) {
+  return 19 * (size_t)g.plane * sizeof(float);
+}
+static inline size_t adj_field_bytes(const StepArgs &g) {
+  return 3 * (size_t)g.cells * sizeof(float);
+}
+
 // Minimum resident 256-thread blocks per SM for the adjoint step: 3 caps it
 // at 80 registers, which measured 7% faster than the unconstrained 102 (more
 // resident warps for the three 76 B/node streams), while 4 (64 registers)
@@ -94,6 +103,9 @@ cudaError_t launch_adjoint_step(const StepArgs &g, const float *lam_in,
   a.grad_force = grad_force;
   a.u_target = nullptr;
   a.partials = nullptr;
+  LBM_CHECK_TABLE(s, chk_r(g.fin, adj_lambda_bytes(g)), chk_r(lam_in, adj_lambda_bytes(g)),
+                  chk_w(lam_out, adj_lambda_bytes(g)), chk_rw(grad_force, adj_field_bytes(g)),
+                  chk_r(g.force, adj_field_bytes(g)));
   const dim3 grid((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz), blk(bx, by, 1);
   const int w = g.walls == 0 ? 0 : g.wall_select ? 1 : 2;
   const bool F = g.force != nullptr, G = grad_force != nullptr;
@@ -130,6 +142,9 @@ cudaError_t launch_adjoint_step_mom(const StepArgs &g, const float *rho_n, const
   a.grad_force = grad_force;
   a.u_target = nullptr;
   a.partials = nullptr;
+  LBM_CHECK_TABLE(s, chk_r(rho_n, adj_field_bytes(g) / 3), chk_r(u_n, adj_field_bytes(g)),
+                  chk_r(lam_in, adj_lambda_bytes(g)), chk_w(lam_out, adj_lambda_bytes(g)),
+                  chk_rw(grad_force, adj_field_bytes(g)), chk_r(g.force, adj_field_bytes(g)));
   const dim3 grid((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz), blk(bx, by, 1);
   const int w = g.walls == 0 ? 0 : g.wall_select ? 1 : 2;
   const bool F = g.force != nullptr, G = grad_force != nullptr;
@@ -166,6 +181,10 @@ cudaError_t launch_adjoint_seed(const StepArgs &g, const float *u_target,
   a.u_target = u_target;
   a.partials = partials;
   const int nb = moments_blocks(g.cells);
+  LBM_CHECK_TABLE(s, chk_r(g.fin, adj_lambda_bytes(g)), chk_r(u_target, adj_field_bytes(g)),
+                  chk_w(lam_out, adj_lambda_bytes(g)), chk_w(grad_force, adj_field_bytes(g)),
+                  chk_r(g.force, adj_field_bytes(g)),
+                  chk_w(partials, (size_t)nb * sizeof(double)));
   if (g.force) k_adjoint_seed<true><<<nb, kReduceThreads, 0, s>>>(a);
   else k_adjoint_seed<false><<<nb, kReduceThreads, 0, s>>>(a);
   return cudaGetLastError();
@@ -175,6 +194,8 @@ cudaError_t launch_adjoint_u0(const StepArgs &g, const float *lam0,
                               const float *u0, float *grad, int bx, int by,
                               cudaStream_t s) {
   const dim3 grid((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz), blk(bx, by, 1);
+  LBM_CHECK_TABLE(s, chk_r(lam0, adj_lambda_bytes(g)), chk_r(u0, adj_field_bytes(g)),
+                  chk_w(grad, adj_field_bytes(g)));
   k_adjoint_u0<<<grid, blk, 0, s>>>(g, lam0, u0, grad);
   return cudaGetLastError();
 }

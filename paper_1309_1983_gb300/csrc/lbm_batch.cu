@@ -19,6 +19,10 @@
 #include "internal.h"
 #include "stream.cuh"
 
+#ifdef LBM_CHECK
+#include <vector>
+#endif
+
 namespace lbm {
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -50,20 +54,19 @@ __device__ bool grid_barrier(const BatchArgs &a) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned *gen = a.bar_gen;
-    const unsigned g0 = *gen;
+    const unsigned g0 = LBM_LDV(a.bar_gen);
     __threadfence();
-    const unsigned arrived = atomicAdd(a.bar_count, 1u) + 1u;
+    const unsigned arrived = LBM_ATOMIC_ADD(a.bar_count, 1u) + 1u;
     int good = 1;
     if (arrived == a.expected) {
-      *a.bar_count = 0u;  // nobody re-arrives before gen moves
+      LBM_ST(a.bar_count, 0u);  // nobody re-arrives before gen moves
       __threadfence();
-      atomicAdd(a.bar_gen, 1u);
+      LBM_ATOMIC_ADD(a.bar_gen, 1u);
     } else {
       const unsigned long long t0 = global_ns();
-      while (*gen == g0) {
+      while (LBM_LDV(a.bar_gen) == g0) {
         if (global_ns() - t0 > a.timeout_ns) {
-          atomicOr(a.err, kErrTimeout);
+          LBM_ATOMIC_OR(a.err, (int)kErrTimeout);
           good = 0;
           break;
         }
@@ -71,7 +74,7 @@ __device__ bool grid_barrier(const BatchArgs &a) {
       }
     }
     __threadfence();
-    if (*(volatile int *)a.err & kErrTimeout) good = 0;
+    if (LBM_LDV(a.err) & kErrTimeout) good = 0;
     ok = good;
   }
   __syncthreads();
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(256) k_batch_persistent(const BatchArgs a) {
     const uint32_t *src = reinterpret_cast<const uint32_t *>(a.doms);
     uint32_t *dst = reinterpret_cast<uint32_t *>(sdoms);
     const int words = a.ndom * (int)(sizeof(BatchDom) / 4);
-    for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+    for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = LBM_LD(&src[k]);
     __syncthreads();
   }
   for (int s = 0; s < a.nsteps; ++s) {
@@ -100,10 +103,10 @@ __global__ void __launch_bounds__(256) k_batch_persistent(const BatchArgs a) {
     const float *fin = odd ? a.f[1] : a.f[0];
     float *fout = odd ? a.f[0] : a.f[1];
     int t = blockIdx.x;
-    int2 tile = t < a.ntiles ? a.tiles[t] : make_int2(0, 0);
+    int2 tile = t < a.ntiles ? LBM_LD(&a.tiles[t]) : make_int2(0, 0);
     for (; t < a.ntiles; t += gridDim.x) {
       const int tn = t + gridDim.x;
-      const int2 next = tn < a.ntiles ? a.tiles[tn] : tile;
+      const int2 next = tn < a.ntiles ? LBM_LD(&a.tiles[tn]) : tile;
       const BatchDom &D = sdoms[tile.x];
       const uint32_t k = (uint32_t)tile.y + threadIdx.x;
       if (k < D.cells) {
@@ -127,7 +130,7 @@ __device__ __forceinline__ BatchDom *stage_domains(const BatchArgs &a) {
   const uint32_t *src = reinterpret_cast<const uint32_t *>(a.doms);
   uint32_t *dst = reinterpret_cast<uint32_t *>(sdoms);
   const int words = a.ndom * (int)(sizeof(BatchDom) / 4);
-  for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+  for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = LBM_LD(&src[k]);
   __syncthreads();
   return sdoms;
 }
@@ -148,10 +151,10 @@ __global__ void __launch_bounds__(256) k_batch_fwd_seq(const BatchArgs a,
     float *rho = MOM ? q.rho[s] : nullptr;
     float *u = MOM ? q.u[s] : nullptr;
     int t = blockIdx.x;
-    int2 tile = t < a.ntiles ? a.tiles[t] : make_int2(0, 0);
+    int2 tile = t < a.ntiles ? LBM_LD(&a.tiles[t]) : make_int2(0, 0);
     for (; t < a.ntiles; t += gridDim.x) {
       const int tn = t + gridDim.x;
-      const int2 next = tn < a.ntiles ? a.tiles[tn] : tile;
+      const int2 next = tn < a.ntiles ? LBM_LD(&a.tiles[tn]) : tile;
       const BatchDom &D = sdoms[tile.x];
       const uint32_t k = (uint32_t)tile.y + threadIdx.x;
       if (k < D.cells) {
@@ -187,10 +190,10 @@ __global__ void __launch_bounds__(256, 4) k_batch_adj_seq(const BatchArgs a,
     const float *rho = q.rho[s];
     const float *u = q.u[s];
     int t = blockIdx.x;
-    int2 tile = t < a.ntiles ? a.tiles[t] : make_int2(0, 0);
+    int2 tile = t < a.ntiles ? LBM_LD(&a.tiles[t]) : make_int2(0, 0);
     for (; t < a.ntiles; t += gridDim.x) {
       const int tn = t + gridDim.x;
-      const int2 next = tn < a.ntiles ? a.tiles[tn] : tile;
+      const int2 next = tn < a.ntiles ? LBM_LD(&a.tiles[tn]) : tile;
       const BatchDom &D = sdoms[tile.x];
       const uint32_t k = (uint32_t)tile.y + threadIdx.x;
       if (k < D.cells) {
@@ -212,7 +215,8 @@ __global__ void __launch_bounds__(256, 4) k_batch_adj_seq(const BatchArgs a,
 template <bool WALLS>
 __global__ void __launch_bounds__(256) k_batch_step(const BatchArgs a, const float *fin,
                                                     float *fout) {
-  const int2 tile = a.tiles[blockIdx.x];
+  const int2 tile = LBM_LD(&a.tiles[blockIdx.x]);
+  if (!LBM_VALID(&a.doms[tile.x])) return;
   const BatchDom &D = a.doms[tile.x];
   const uint32_t k = (uint32_t)tile.y + threadIdx.x;
   if (k >= D.cells) return;
@@ -228,7 +232,8 @@ __global__ void __launch_bounds__(256) k_batch_step(const BatchArgs a, const flo
 template <bool WALLS>
 __global__ void __launch_bounds__(256) k_batch_step_mom(const BatchArgs a, const float *fin,
                                                         float *fout, float *rho, float *u) {
-  const int2 tile = a.tiles[blockIdx.x];
+  const int2 tile = LBM_LD(&a.tiles[blockIdx.x]);
+  if (!LBM_VALID(&a.doms[tile.x])) return;
   const BatchDom &D = a.doms[tile.x];
   const uint32_t k = (uint32_t)tile.y + threadIdx.x;
   if (k >= D.cells) return;
@@ -242,21 +247,23 @@ __global__ void __launch_bounds__(256) k_batch_step_mom(const BatchArgs a, const
 
 // f = w_i (shifted value 0) on every node of every domain.
 __global__ void __launch_bounds__(256) k_batch_rest(const BatchArgs a, float *f) {
-  const int2 tile = a.tiles[blockIdx.x];
+  const int2 tile = LBM_LD(&a.tiles[blockIdx.x]);
+  if (!LBM_VALID(&a.doms[tile.x])) return;
   const BatchDom &D = a.doms[tile.x];
   const uint32_t k = (uint32_t)tile.y + threadIdx.x;
   if (k >= D.cells) return;
   int x, y, z;
   decode(D, k, x, y, z);
   const uint32_t c = ((uint32_t)z * D.ny + y) * D.pitch + x;
-  for (int i = 0; i < Q; ++i) f[D.foff + (size_t)i * D.plane + c] = 0.0f;
+  for (int i = 0; i < Q; ++i) LBM_ST(&f[D.foff + (size_t)i * D.plane + c], 0.0f);
 }
 
 // rho and u of every node into dense per-domain blocks:
 // rho[coff + k], u[3 * coff + comp * cells + k].
 __global__ void __launch_bounds__(256) k_batch_moments(const BatchArgs a, const float *f,
                                                        float *rho, float *u) {
-  const int2 tile = a.tiles[blockIdx.x];
+  const int2 tile = LBM_LD(&a.tiles[blockIdx.x]);
+  if (!LBM_VALID(&a.doms[tile.x])) return;
   const BatchDom &D = a.doms[tile.x];
   const uint32_t k = (uint32_t)tile.y + threadIdx.x;
   if (k >= D.cells) return;
@@ -266,17 +273,17 @@ __global__ void __launch_bounds__(256) k_batch_moments(const BatchArgs a, const 
   float d[Q];
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    d[i] = __ldg(f + D.foff + (size_t)i * D.plane + c);
+    d[i] = LBM_LDG(f + D.foff + (size_t)i * D.plane + c);
   });
   float dr, jx, jy, jz;
   shifted_moments(d, dr, jx, jy, jz);
   const float r = 1.0f + dr, rinv = __frcp_rn(r);
-  if (rho) rho[D.coff + k] = r;
+  if (rho) LBM_ST(&rho[D.coff + k], r);
   if (u) {
     float *ud = u + 3 * (size_t)D.coff;
-    ud[k] = jx * rinv;
-    ud[D.cells + k] = jy * rinv;
-    ud[2 * (size_t)D.cells + k] = jz * rinv;
+    LBM_ST(&ud[k], jx * rinv);
+    LBM_ST(&ud[D.cells + k], jy * rinv);
+    LBM_ST(&ud[2 * (size_t)D.cells + k], jz * rinv);
   }
 }
 
@@ -284,7 +291,8 @@ __global__ void __launch_bounds__(256) k_batch_moments(const BatchArgs a, const 
 // dense per-domain blocks: u0[3 * coff + comp * cells + node].
 __global__ void __launch_bounds__(256) k_batch_init_eq(const BatchArgs a, float *f,
                                                        const float *u0) {
-  const int2 tile = a.tiles[blockIdx.x];
+  const int2 tile = LBM_LD(&a.tiles[blockIdx.x]);
+  if (!LBM_VALID(&a.doms[tile.x])) return;
   const BatchDom &D = a.doms[tile.x];
   const uint32_t k = (uint32_t)tile.y + threadIdx.x;
   if (k >= D.cells) return;
@@ -294,15 +302,15 @@ __global__ void __launch_bounds__(256) k_batch_init_eq(const BatchArgs a, float 
   float ux = 0.f, uy = 0.f, uz = 0.f;
   if (u0) {
     const float *ud = u0 + 3 * (size_t)D.coff;
-    ux = ud[k];
-    uy = ud[D.cells + k];
-    uz = ud[2 * (size_t)D.cells + k];
+    ux = LBM_LD(&ud[k]);
+    uy = LBM_LD(&ud[D.cells + k]);
+    uz = LBM_LD(&ud[2 * (size_t)D.cells + k]);
   }
   float d[Q];
   shifted_equilibrium(1.0f, ux, uy, uz, d);
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    f[D.foff + (size_t)i * D.plane + c] = d[i];
+    LBM_ST(&f[D.foff + (size_t)i * D.plane + c], d[i]);
   });
 }
 
@@ -319,7 +327,8 @@ template <bool GRADF>
 __global__ void __launch_bounds__(256, LBM_BATCH_ADJ_MIN_BLOCKS)
     k_batch_adjoint_step(const BatchArgs a, const float *fn, const float *lam_in,
                          float *lam_out, float *gF) {
-  const int2 tile = a.tiles[blockIdx.x];
+  const int2 tile = LBM_LD(&a.tiles[blockIdx.x]);
+  if (!LBM_VALID(&a.doms[tile.x])) return;
   const BatchDom &D = a.doms[tile.x];
   const uint32_t k = (uint32_t)tile.y + threadIdx.x;
   if (k >= D.cells) return;
@@ -338,7 +347,8 @@ template <bool GRADF>
 __global__ void __launch_bounds__(256)
     k_batch_adjoint_step_mom(const BatchArgs a, const float *rho, const float *u,
                              const float *lam_in, float *lam_out, float *gF) {
-  const int2 tile = a.tiles[blockIdx.x];
+  const int2 tile = LBM_LD(&a.tiles[blockIdx.x]);
+  if (!LBM_VALID(&a.doms[tile.x])) return;
   const BatchDom &D = a.doms[tile.x];
   const uint32_t k = (uint32_t)tile.y + threadIdx.x;
   if (k >= D.cells) return;
@@ -355,7 +365,8 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_batch_adjoint_seed(const BatchArgs a, const float *fT, const float *ut, float *lam,
                          float *gF, double *partials) {
-  const int2 tile = a.tiles[blockIdx.x];
+  const int2 tile = LBM_LD(&a.tiles[blockIdx.x]);
+  if (!LBM_VALID(&a.doms[tile.x])) return;
   const BatchDom &D = a.doms[tile.x];
   const uint32_t k = (uint32_t)tile.y + threadIdx.x;
   double acc = 0.0;
@@ -371,7 +382,8 @@ __global__ void __launch_bounds__(256)
 
 __global__ void __launch_bounds__(256)
     k_batch_adjoint_u0(const BatchArgs a, const float *lam0, const float *u0, float *grad) {
-  const int2 tile = a.tiles[blockIdx.x];
+  const int2 tile = LBM_LD(&a.tiles[blockIdx.x]);
+  if (!LBM_VALID(&a.doms[tile.x])) return;
   const BatchDom &D = a.doms[tile.x];
   const uint32_t k = (uint32_t)tile.y + threadIdx.x;
   if (k >= D.cells) return;
@@ -402,6 +414,8 @@ cudaError_t launch_batch_persistent(const BatchArgs &a, int grid, int threads,
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  LBM_CHECK_TABLE(s, LBM_BATCH_RANGES(a), chk_rw(a.f[0], LBM_BATCH_F(a)),
+                  chk_rw(a.f[1], LBM_BATCH_F(a)));
   if (a.walls_any)
     return cudaLaunchKernelEx(&cfg, k_batch_persistent<true>, a);
   return cudaLaunchKernelEx(&cfg, k_batch_persistent<false>, a);
@@ -438,6 +452,21 @@ cudaError_t launch_batch_fwd_seq(const BatchArgs &a, const BatchFwdSeq &q, int g
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = coop_config(grid, threads, batch_persistent_smem(a.ndom), s, attr);
   const bool mom = q.rho[0] != nullptr;
+#ifdef LBM_CHECK
+  {
+    std::vector<CheckRange> r = {LBM_BATCH_RANGES(a)};
+    for (int k = 0; k < q.n; ++k) {
+      r.push_back(chk_r(q.fin[k], LBM_BATCH_F(a)));
+      r.push_back(chk_w(q.fout[k], LBM_BATCH_F(a)));
+      if (mom) {
+        r.push_back(chk_w(q.rho[k], LBM_BATCH_FIELD(a, 1)));
+        r.push_back(chk_w(q.u[k], LBM_BATCH_FIELD(a, 3)));
+      }
+    }
+    const cudaError_t ce = check_table(s, r.data(), (int)r.size());
+    if (ce != cudaSuccess) return ce;
+  }
+#endif
   if (a.walls_any)
     return mom ? cudaLaunchKernelEx(&cfg, k_batch_fwd_seq<true, true>, a, q)
                : cudaLaunchKernelEx(&cfg, k_batch_fwd_seq<true, false>, a, q);
@@ -449,12 +478,27 @@ cudaError_t launch_batch_adj_seq(const BatchArgs &a, const BatchAdjSeq &q, int g
                                  cudaStream_t s) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = coop_config(grid, threads, batch_persistent_smem(a.ndom), s, attr);
+#ifdef LBM_CHECK
+  {
+    std::vector<CheckRange> r = {LBM_BATCH_RANGES(a), chk_rw(q.lam[0], LBM_BATCH_F(a)),
+                                 chk_rw(q.lam[1], LBM_BATCH_F(a)),
+                                 chk_rw(q.gF, LBM_BATCH_FIELD(a, 3))};
+    for (int k = 0; k < q.n; ++k) {
+      r.push_back(chk_r(q.rho[k], LBM_BATCH_FIELD(a, 1)));
+      r.push_back(chk_r(q.u[k], LBM_BATCH_FIELD(a, 3)));
+    }
+    const cudaError_t ce = check_table(s, r.data(), (int)r.size());
+    if (ce != cudaSuccess) return ce;
+  }
+#endif
   if (q.gF) return cudaLaunchKernelEx(&cfg, k_batch_adj_seq<true>, a, q);
   return cudaLaunchKernelEx(&cfg, k_batch_adj_seq<false>, a, q);
 }
 
 cudaError_t launch_batch_step(const BatchArgs &a, const float *fin, float *fout,
                               int threads, cudaStream_t s) {
+  LBM_CHECK_TABLE(s, LBM_BATCH_RANGES(a), chk_r(fin, LBM_BATCH_F(a)),
+                  chk_w(fout, LBM_BATCH_F(a)));
   if (a.walls_any)
     k_batch_step<true><<<a.ntiles, threads, 0, s>>>(a, fin, fout);
   else
@@ -464,6 +508,8 @@ cudaError_t launch_batch_step(const BatchArgs &a, const float *fin, float *fout,
 
 cudaError_t launch_batch_step_mom(const BatchArgs &a, const float *fin, float *fout, float *rho,
                                   float *u, int threads, cudaStream_t s) {
+  LBM_CHECK_TABLE(s, LBM_BATCH_RANGES(a), chk_r(fin, LBM_BATCH_F(a)), chk_w(fout, LBM_BATCH_F(a)),
+                  chk_w(rho, LBM_BATCH_FIELD(a, 1)), chk_w(u, LBM_BATCH_FIELD(a, 3)));
   if (a.walls_any)
     k_batch_step_mom<true><<<a.ntiles, threads, 0, s>>>(a, fin, fout, rho, u);
   else
@@ -474,6 +520,9 @@ cudaError_t launch_batch_step_mom(const BatchArgs &a, const float *fin, float *f
 cudaError_t launch_batch_adjoint_step_mom(const BatchArgs &a, const float *rho, const float *u,
                                           const float *lam_in, float *lam_out, float *gF,
                                           int threads, cudaStream_t s) {
+  LBM_CHECK_TABLE(s, LBM_BATCH_RANGES(a), chk_r(rho, LBM_BATCH_FIELD(a, 1)),
+                  chk_r(u, LBM_BATCH_FIELD(a, 3)), chk_r(lam_in, LBM_BATCH_F(a)),
+                  chk_w(lam_out, LBM_BATCH_F(a)), chk_rw(gF, LBM_BATCH_FIELD(a, 3)));
   if (gF)
     k_batch_adjoint_step_mom<true><<<a.ntiles, threads, 0, s>>>(a, rho, u, lam_in, lam_out, gF);
   else
@@ -483,24 +532,32 @@ cudaError_t launch_batch_adjoint_step_mom(const BatchArgs &a, const float *rho, 
 }
 
 cudaError_t launch_batch_rest(const BatchArgs &a, float *f, int threads, cudaStream_t s) {
+  LBM_CHECK_TABLE(s, LBM_BATCH_RANGES(a), chk_w(f, LBM_BATCH_F(a)));
   k_batch_rest<<<a.ntiles, threads, 0, s>>>(a, f);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_moments(const BatchArgs &a, const float *f, float *rho, float *u,
                                  int threads, cudaStream_t s) {
+  LBM_CHECK_TABLE(s, LBM_BATCH_RANGES(a), chk_r(f, LBM_BATCH_F(a)),
+                  chk_w(rho, LBM_BATCH_FIELD(a, 1)), chk_w(u, LBM_BATCH_FIELD(a, 3)));
   k_batch_moments<<<a.ntiles, threads, 0, s>>>(a, f, rho, u);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_init_eq(const BatchArgs &a, float *f, const float *u0, int threads,
                                  cudaStream_t s) {
+  LBM_CHECK_TABLE(s, LBM_BATCH_RANGES(a), chk_w(f, LBM_BATCH_F(a)),
+                  chk_r(u0, LBM_BATCH_FIELD(a, 3)));
   k_batch_init_eq<<<a.ntiles, threads, 0, s>>>(a, f, u0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_adjoint_step(const BatchArgs &a, const float *fn, const float *lam_in,
                                       float *lam_out, float *gF, int threads, cudaStream_t s) {
+  LBM_CHECK_TABLE(s, LBM_BATCH_RANGES(a), chk_r(fn, LBM_BATCH_F(a)),
+                  chk_r(lam_in, LBM_BATCH_F(a)), chk_w(lam_out, LBM_BATCH_F(a)),
+                  chk_rw(gF, LBM_BATCH_FIELD(a, 3)));
   if (gF)
     k_batch_adjoint_step<true><<<a.ntiles, threads, 0, s>>>(a, fn, lam_in, lam_out, gF);
   else
@@ -511,12 +568,18 @@ cudaError_t launch_batch_adjoint_step(const BatchArgs &a, const float *fn, const
 cudaError_t launch_batch_adjoint_seed(const BatchArgs &a, const float *fT, const float *ut,
                                       float *lam, float *gF, double *partials, int threads,
                                       cudaStream_t s) {
+  LBM_CHECK_TABLE(s, LBM_BATCH_RANGES(a), chk_r(fT, LBM_BATCH_F(a)),
+                  chk_r(ut, LBM_BATCH_FIELD(a, 3)), chk_w(lam, LBM_BATCH_F(a)),
+                  chk_w(gF, LBM_BATCH_FIELD(a, 3)),
+                  chk_w(partials, (size_t)a.ntiles * sizeof(double)));
   k_batch_adjoint_seed<<<a.ntiles, threads, 0, s>>>(a, fT, ut, lam, gF, partials);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_adjoint_u0(const BatchArgs &a, const float *lam0, const float *u0,
                                     float *grad, int threads, cudaStream_t s) {
+  LBM_CHECK_TABLE(s, LBM_BATCH_RANGES(a), chk_r(lam0, LBM_BATCH_F(a)),
+                  chk_r(u0, LBM_BATCH_FIELD(a, 3)), chk_w(grad, LBM_BATCH_FIELD(a, 3)));
   k_batch_adjoint_u0<<<a.ntiles, threads, 0, s>>>(a, lam0, u0, grad);
   return cudaGetLastError();
 }

@@ -182,6 +182,10 @@ BatchArgs make_args(const lbm_batch *b) {
   memset(&a, 0, sizeof(a));
   a.f[0] = b->f[0];
   a.f[1] = b->f[1];
+#ifdef LBM_CHECK
+  a.f_elems = b->f_elems;
+  a.cells = (uint32_t)b->cells;
+#endif
   a.doms = b->d_doms;
   a.tiles = b->d_tiles;
   a.ntiles = (int)b->tiles.size();
@@ -223,6 +227,9 @@ int lbm_batch_create(int ndom, const int *dims, const float *tau, const float *l
                      uint32_t flags, lbm_batch_t **out) {
   if (!out) return bfail(LBM_EINVAL, "out is NULL");
   *out = nullptr;
+#ifdef LBM_CHECK
+  if (!lbm::check_record()) return bfail(LBM_ENOMEM, "check record allocation failed");
+#endif
   if (ndom < 1 || !dims || !tau) return bfail(LBM_EINVAL, "need ndom >= 1, dims, tau");
   if (ndom > lbm::kMaxBatchDomains) return bfail(LBM_ERANGE, "at most 256 domains per batch");
   const uint32_t known = LBM_WALL_X | LBM_WALL_Y | LBM_WALL_Z | LBM_LID;

@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "d3q19.cuh"
@@ -296,6 +297,26 @@ void host_from_float(void *base, size_t k, int storage, float v) {
 namespace lbm {
 int set_error(int code, const char *what) { return fail(code, what); }
 int set_cuda_error(cudaError_t e, const char *where) { return cuda_fail(e, where); }
+
+#ifdef LBM_CHECK
+// The refused-access record of the check build: allocated and zeroed once,
+// on the first handle creation (before any stream capture, during which a
+// cudaMalloc is not allowed), and kept for the life of the process.
+CheckRecord *check_record() {
+  static CheckRecord *rec = [] {
+    CheckRecord *p = nullptr;
+    if (cudaMalloc(&p, sizeof(CheckRecord)) != cudaSuccess) return (CheckRecord *)nullptr;
+    if (cudaMemset(p, 0, sizeof(CheckRecord)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+      return (CheckRecord *)nullptr;
+    return p;
+  }();
+  return rec;
+}
+
+static std::atomic<size_t> g_check_narrow{0};
+size_t check_narrow_bytes() { return g_check_narrow.load(); }
+#endif
 }  // namespace lbm
 
 extern "C" {
@@ -310,6 +331,7 @@ const char *lbm_strerror(int code) {
     case LBM_ENONFINITE: return "LBM_ENONFINITE: non-finite density";
     case LBM_EUNBOUND: return "LBM_EUNBOUND: no buffers bound";
     case LBM_ERANGE: return "LBM_ERANGE: size above the supported maximum";
+    case LBM_ENOTSUP: return "LBM_ENOTSUP: not in this build";
     default: return "LBM: unknown status code";
   }
 }
@@ -320,6 +342,9 @@ int lbm_create(int nx, int ny, int nz, float tau, uint32_t flags,
                lbm_t **out) {
   if (!out) return fail(LBM_EINVAL, "out is NULL");
   *out = nullptr;
+#ifdef LBM_CHECK
+  if (!lbm::check_record()) return fail(LBM_ENOMEM, "check record allocation failed");
+#endif
   if (nx < 1 || ny < 1 || nz < 1) return fail(LBM_EINVAL, "sizes must be >= 1");
   if (!(tau > 0.5f) || !isfinite(tau)) return fail(LBM_EINVAL, "tau must be > 1/2");
   if (flags & ~kKnownFlags) return fail(LBM_EINVAL, "unknown flag bits");
@@ -881,6 +906,48 @@ int lbm_adjoint_u0(lbm_t *h, const float *lambda0, const float *u0,
   cudaError_t e = lbm::launch_adjoint_u0(g, lambda0, u0, grad_u0, h->bx, h->by, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint u0 launch");
   return LBM_OK;
+}
+
+int lbm_check_status(unsigned long long *refused, unsigned long long *first_addr,
+                     unsigned int *first_bytes, unsigned int *first_kind) {
+#ifdef LBM_CHECK
+  lbm::CheckRecord r = {};
+  lbm::CheckRecord *d = lbm::check_record();
+  if (!d) return fail(LBM_ENOMEM, "check record allocation failed");
+  LBM_CUDA(cudaDeviceSynchronize(), "check status sync");
+  LBM_CUDA(cudaMemcpy(&r, d, sizeof(r), cudaMemcpyDeviceToHost), "check status copy");
+  if (refused) *refused = r.count;
+  if (first_addr) *first_addr = r.first;
+  if (first_bytes) *first_bytes = r.first_bytes;
+  if (first_kind) *first_kind = r.first_kind;
+  return LBM_OK;
+#else
+  (void)refused, (void)first_addr, (void)first_bytes, (void)first_kind;
+  return fail(LBM_ENOTSUP, "built without LBM_CHECK");
+#endif
+}
+
+int lbm_check_reset(void) {
+#ifdef LBM_CHECK
+  lbm::CheckRecord *d = lbm::check_record();
+  if (!d) return fail(LBM_ENOMEM, "check record allocation failed");
+  LBM_CUDA(cudaDeviceSynchronize(), "check reset sync");
+  LBM_CUDA(cudaMemset(d, 0, sizeof(lbm::CheckRecord)), "check reset");
+  LBM_CUDA(cudaDeviceSynchronize(), "check reset sync");
+  return LBM_OK;
+#else
+  return fail(LBM_ENOTSUP, "built without LBM_CHECK");
+#endif
+}
+
+int lbm_check_narrow(size_t bytes) {
+#ifdef LBM_CHECK
+  lbm::g_check_narrow.store(bytes);
+  return LBM_OK;
+#else
+  (void)bytes;
+  return fail(LBM_ENOTSUP, "built without LBM_CHECK");
+#endif
 }
 
 }  // extern "C"

@@ -104,6 +104,9 @@ extern "C" int lbm_moments_noalloc(const void *f, int nx, int ny, int nz, uint32
                                    const float *force, float *rho, float *u, double *mass,
                                    void *stream) {
   if (!f) return lbm::set_error(LBM_EINVAL, "f is NULL");
+#ifdef LBM_CHECK
+  if (!lbm::check_record()) return lbm::set_error(LBM_ENOMEM, "check record allocation failed");
+#endif
   if (nx < 1 || ny < 1 || nz < 1) return lbm::set_error(LBM_EINVAL, "sizes must be >= 1");
   const uint32_t st = flags & (LBM_STORE_F16 | LBM_STORE_BF16);
   if (st == (LBM_STORE_F16 | LBM_STORE_BF16))

@@ -47,9 +47,9 @@ __global__ void __launch_bounds__(256) k_step_push(const StepArgs a) {
   const uint32_t dc = ((uint32_t)z * a.ny + y) * a.nx + x;
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
   if constexpr (FORCE) {
-    Fx = __ldg(a.force + dc);
-    Fy = __ldg(a.force + a.cells + dc);
-    Fz = __ldg(a.force + 2 * (size_t)a.cells + dc);
+    Fx = LBM_LDG(a.force + dc);
+    Fy = LBM_LDG(a.force + a.cells + dc);
+    Fz = LBM_LDG(a.force + 2 * (size_t)a.cells + dc);
   }
   float rho, ux, uy, uz;
   collide<FORCE>(d, a.omega, a.kf, Fx, Fy, Fz, rho, ux, uy, uz);
@@ -120,6 +120,7 @@ static void push_dispatch(const StepArgs &a, dim3 g, dim3 b, cudaStream_t s) {
 
 cudaError_t launch_step_push(int storage, const StepArgs &a, int bx, int by, cudaStream_t s) {
   const dim3 g((a.nx + bx - 1) / bx, (a.ny + by - 1) / by, a.nz), b(bx, by, 1);
+  LBM_CHECK_TABLE(s, LBM_STEP_RANGES(a, elem_bytes_of(storage)));
   switch (storage) {
     case kF32: push_dispatch<0>(a, g, b, s); break;
     case kF16: push_dispatch<1>(a, g, b, s); break;
@@ -132,6 +133,7 @@ cudaError_t launch_step_push(int storage, const StepArgs &a, int bx, int by, cud
 cudaError_t launch_stream(int storage, const StepArgs &a, int form, int bx, int by,
                           cudaStream_t s) {
   const dim3 g((a.nx + bx - 1) / bx, (a.ny + by - 1) / by, a.nz), b(bx, by, 1);
+  LBM_CHECK_TABLE(s, LBM_STEP_RANGES(a, elem_bytes_of(storage)));
   switch (storage) {
     case kF32: k_stream<0><<<g, b, 0, s>>>(a, form); break;
     case kF16: k_stream<1><<<g, b, 0, s>>>(a, form); break;

@@ -48,9 +48,9 @@ __global__ void LBM_STEP_BOUNDS k_step(const StepArgs a) {
     const uint32_t dc = ((uint32_t)z * a.ny + y) * a.nx + x;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
     if constexpr (FORCE) {
-      Fx = __ldg(a.force + dc);
-      Fy = __ldg(a.force + a.cells + dc);
-      Fz = __ldg(a.force + 2 * (size_t)a.cells + dc);
+      Fx = LBM_LDG(a.force + dc);
+      Fy = LBM_LDG(a.force + a.cells + dc);
+      Fz = LBM_LDG(a.force + 2 * (size_t)a.cells + dc);
     }
     if (on_wall(n)) onsite_apply<S>(fin, a, n, Fx, Fy, Fz, d);
     float rho, ux, uy, uz;
@@ -60,10 +60,10 @@ __global__ void LBM_STEP_BOUNDS k_step(const StepArgs a) {
       Store<S>::st(fout + (size_t)i * a.plane + n.c, d[i]);
     });
     if constexpr (MOM) {
-      a.rho[dc] = rho;
-      a.u[dc] = ux;
-      a.u[a.cells + dc] = uy;
-      a.u[2 * (size_t)a.cells + dc] = uz;
+      LBM_ST(&a.rho[dc], rho);
+      LBM_ST(&a.u[dc], ux);
+      LBM_ST(&a.u[a.cells + dc], uy);
+      LBM_ST(&a.u[2 * (size_t)a.cells + dc], uz);
     }
   } else {
     step_node<S, (W != 0), FORCE, MOM, false>(
@@ -84,12 +84,12 @@ __global__ void __launch_bounds__(256)
   if (x >= a.nx || y >= a.ny) return;
   const uint32_t c = ((uint32_t)z * a.ny + y) * a.pitch + x;
   const uint32_t dc = ((uint32_t)z * a.ny + y) * a.nx + x;
-  const float r = rho0 ? rho0[dc] : 1.0f;
+  const float r = rho0 ? LBM_LD(&rho0[dc]) : 1.0f;
   float ux = 0.f, uy = 0.f, uz = 0.f;
   if (u0) {
-    ux = u0[dc];
-    uy = u0[a.cells + dc];
-    uz = u0[2 * (size_t)a.cells + dc];
+    ux = LBM_LD(&u0[dc]);
+    uy = LBM_LD(&u0[a.cells + dc]);
+    uz = LBM_LD(&u0[2 * (size_t)a.cells + dc]);
   }
   float d[Q];
   shifted_equilibrium(r, ux, uy, uz, d);
@@ -128,16 +128,16 @@ __global__ void __launch_bounds__(kReduceThreads)
     shifted_moments(d, dr, jx, jy, jz);
     const float r = 1.0f + dr;
     if constexpr (FORCE) {
-      jx = fmaf(-0.5f, __ldg(a.force + dc), jx);
-      jy = fmaf(-0.5f, __ldg(a.force + a.cells + dc), jy);
-      jz = fmaf(-0.5f, __ldg(a.force + 2 * (size_t)a.cells + dc), jz);
+      jx = fmaf(-0.5f, LBM_LDG(a.force + dc), jx);
+      jy = fmaf(-0.5f, LBM_LDG(a.force + a.cells + dc), jy);
+      jz = fmaf(-0.5f, LBM_LDG(a.force + 2 * (size_t)a.cells + dc), jz);
     }
     const float rinv = __frcp_rn(r);
-    if (rho) rho[dc] = r;
+    if (rho) LBM_ST(&rho[dc], r);
     if (u) {
-      u[dc] = jx * rinv;
-      u[a.cells + dc] = jy * rinv;
-      u[2 * (size_t)a.cells + dc] = jz * rinv;
+      LBM_ST(&u[dc], jx * rinv);
+      LBM_ST(&u[a.cells + dc], jy * rinv);
+      LBM_ST(&u[2 * (size_t)a.cells + dc], jz * rinv);
     }
     acc += (double)dr;
     bad |= !isfinite(r);
@@ -148,11 +148,11 @@ __global__ void __launch_bounds__(kReduceThreads)
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = acc;
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, kErrNonFinite);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) LBM_ATOMIC_OR(err, (int)kErrNonFinite);
   if (wid == 0) {
     acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) partials[blockIdx.x] = acc;
+    if (lane == 0) LBM_ST(&partials[blockIdx.x], acc);
   }
 }
 
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(1024)
                double *__restrict__ out) {
   __shared__ double red[32];
   double acc = 0.0;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) acc += LBM_LD(&partials[k]);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = acc;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(1024)
   if (wid == 0) {
     acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) *out = offset + acc;
+    if (lane == 0) LBM_ST(out, offset + acc);
   }
 }
 
@@ -211,6 +211,7 @@ static void step_dispatch(bool moments, const StepArgs &a, dim3 g, dim3 b,
 cudaError_t launch_step(int storage, bool moments, const StepArgs &a, int bx,
                         int by, cudaStream_t s) {
   const dim3 g = node_grid(a, bx, by), b(bx, by, 1);
+  LBM_CHECK_TABLE(s, LBM_STEP_RANGES(a, elem_bytes_of(storage)));
   switch (storage) {
     case kF32: step_dispatch<0>(moments, a, g, b, s); break;
     case kF16: step_dispatch<1>(moments, a, g, b, s); break;
@@ -223,6 +224,9 @@ cudaError_t launch_step(int storage, bool moments, const StepArgs &a, int bx,
 cudaError_t launch_init(int storage, const StepArgs &a, const float *rho0,
                         const float *u0, int bx, int by, cudaStream_t s) {
   const dim3 g = node_grid(a, bx, by), b(bx, by, 1);
+  LBM_CHECK_TABLE(s, chk_w(a.fout, 19 * (size_t)a.plane * elem_bytes_of(storage)),
+                  chk_r(rho0, (size_t)a.cells * sizeof(float)),
+                  chk_r(u0, 3 * (size_t)a.cells * sizeof(float)));
   switch (storage) {
     case kF32: k_init<0><<<g, b, 0, s>>>(a, rho0, u0); break;
     case kF16: k_init<1><<<g, b, 0, s>>>(a, rho0, u0); break;
@@ -251,6 +255,11 @@ cudaError_t launch_moments(int storage, const StepArgs &a, const void *f,
   if (nb < 1) nb = 1;
   double *partials = scr ? scr->partials : nullptr;
   int *err = scr ? scr->err : nullptr;
+  LBM_CHECK_TABLE(s, chk_r(f, 19 * (size_t)a.plane * elem_bytes_of(storage)),
+                  chk_w(rho, (size_t)a.cells * sizeof(float)),
+                  chk_w(u, 3 * (size_t)a.cells * sizeof(float)),
+                  chk_r(a.force, 3 * (size_t)a.cells * sizeof(float)),
+                  chk_w(partials, (size_t)nb * sizeof(double)), chk_rw(err, sizeof(int)));
   switch (storage) {
     case kF32: moments_dispatch<0>(a, f, rho, u, partials, err, nb, s); break;
     case kF16: moments_dispatch<1>(a, f, rho, u, partials, err, nb, s); break;
@@ -268,6 +277,8 @@ int moments_blocks(uint32_t cells) {
 
 cudaError_t launch_finalize_sum(const Scratch &scr, int nparts, double offset,
                                 double *out, cudaStream_t s) {
+  LBM_CHECK_TABLE(s, chk_r(scr.partials, (size_t)nparts * sizeof(double)),
+                  chk_w(out, sizeof(double)));
   k_finalize<<<1, 1024, 0, s>>>(scr.partials, nparts, offset, out);
   return cudaGetLastError();
 }

@@ -72,7 +72,7 @@ __device__ __forceinline__ void pair_node(uint32_t (&V)[Q], const unsigned short
       static_for<1, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         if (bounces<i>(n)) {
-          float v = Pair16<S>::one(__ldg(fin + (size_t)kOpp_v<i> * a.plane + n.c));
+          float v = Pair16<S>::one(LBM_LDG(fin + (size_t)kOpp_v<i> * a.plane + n.c));
           if constexpr (kEz[i] == -1) v += n.z1 ? a.lidc[i] : 0.0f;
           d[i] = v;
         }
@@ -82,9 +82,9 @@ __device__ __forceinline__ void pair_node(uint32_t (&V)[Q], const unsigned short
   const uint32_t dc = ((uint32_t)z * a.ny + y) * a.nx + x;
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
   if constexpr (FORCE) {
-    Fx = __ldg(a.force + dc);
-    Fy = __ldg(a.force + a.cells + dc);
-    Fz = __ldg(a.force + 2 * (size_t)a.cells + dc);
+    Fx = LBM_LDG(a.force + dc);
+    Fy = LBM_LDG(a.force + a.cells + dc);
+    Fz = LBM_LDG(a.force + 2 * (size_t)a.cells + dc);
   }
   float rho, ux, uy, uz;
   collide<FORCE>(d, a.omega, a.kf, Fx, Fy, Fz, rho, ux, uy, uz);
@@ -94,10 +94,10 @@ __device__ __forceinline__ void pair_node(uint32_t (&V)[Q], const unsigned short
     V[i] = H == 0 ? ((V[i] & 0xffff0000u) | b) : ((V[i] & 0x0000ffffu) | (b << 16));
   });
   if constexpr (MOM) {
-    a.rho[dc] = rho;
-    a.u[dc] = ux;
-    a.u[a.cells + dc] = uy;
-    a.u[2 * (size_t)a.cells + dc] = uz;
+    LBM_ST(&a.rho[dc], rho);
+    LBM_ST(&a.u[dc], ux);
+    LBM_ST(&a.u[a.cells + dc], uy);
+    LBM_ST(&a.u[2 * (size_t)a.cells + dc], uz);
   }
 }
 
@@ -129,23 +129,23 @@ __global__ void LBM_PAIR_BOUNDS k_step_pair(const StepArgs a) {
     constexpr int i = decltype(I)::value;
     constexpr int ex = kEx[i], jy = 1 + kEy[i], jz = 1 + kEz[i];
     const unsigned short *row = fin + (size_t)i * a.plane + n0.zo[jz] + n0.yo[jy];
-    const uint32_t P = __ldg(reinterpret_cast<const unsigned int *>(row + xc));
+    const uint32_t P = LBM_LDG(reinterpret_cast<const unsigned int *>(row + xc));
     if constexpr (ex == 0) {
       V[i] = P;
     } else if constexpr (ex == 1) {
       // (x0 - 1, x0): high half of the pair at x0 - 2, low half of P
       uint32_t Pp = __shfl_up_sync(kFull, P, 1);
       if (lane == 0)
-        Pp = x0 >= 2 ? __ldg(reinterpret_cast<const unsigned int *>(row + xl))
-                     : ((uint32_t)__ldg(row + nx - 1) << 16);  // periodic: x = -1
+        Pp = x0 >= 2 ? LBM_LDG(reinterpret_cast<const unsigned int *>(row + xl))
+                     : ((uint32_t)LBM_LDG(row + nx - 1) << 16);  // periodic: x = -1
       V[i] = __byte_perm(Pp, P, 0x5432);
     } else {
       // (x0 + 1, x0 + 2): high half of P, low half of the pair at x0 + 2
       uint32_t Pn = __shfl_down_sync(kFull, P, 1);
-      if (lane == 31) Pn = __ldg(reinterpret_cast<const unsigned int *>(row + xr));
+      if (lane == 31) Pn = LBM_LDG(reinterpret_cast<const unsigned int *>(row + xr));
       uint32_t v = __byte_perm(P, Pn, 0x5432);
-      if (x0 + 2 == nx) v = (v & 0x0000ffffu) | ((uint32_t)__ldg(row) << 16);  // x = nx
-      if (x0 + 1 == nx) v = (v & 0xffff0000u) | (uint32_t)__ldg(row);          // x = nx
+      if (x0 + 2 == nx) v = (v & 0x0000ffffu) | ((uint32_t)LBM_LDG(row) << 16);  // x = nx
+      if (x0 + 1 == nx) v = (v & 0xffff0000u) | (uint32_t)LBM_LDG(row);          // x = nx
       V[i] = v;
     }
   });
@@ -159,7 +159,7 @@ __global__ void LBM_PAIR_BOUNDS k_step_pair(const StepArgs a) {
   // the high half of the last pair of an odd-length row lands in the padding
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    __stcs(reinterpret_cast<unsigned int *>(fout + (size_t)i * a.plane + n0.c - n0.xo[1] + x0),
+    LBM_STCS(reinterpret_cast<unsigned int *>(fout + (size_t)i * a.plane + n0.c - n0.xo[1] + x0),
            V[i]);
   });
 }
@@ -187,6 +187,7 @@ cudaError_t launch_step_pair16(int storage, bool moments, const StepArgs &a, int
                                cudaStream_t s) {
   const int pairs = (a.nx + 1) / 2;
   const dim3 g((pairs + bxp - 1) / bxp, (a.ny + by - 1) / by, a.nz), b(bxp, by, 1);
+  LBM_CHECK_TABLE(s, LBM_STEP_RANGES(a, elem_bytes_of(storage)));
   switch (storage) {
     case kF16: pair_dispatch<1>(moments, a, g, b, s); break;
     case kBF16: pair_dispatch<2>(moments, a, g, b, s); break;

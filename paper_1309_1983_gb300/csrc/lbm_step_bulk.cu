@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(bulk::kThreads) k_step_bulk(const BulkArgs A) 
     for (int t = blockIdx.x; t < A.ntiles && ok; t += gridDim.x, ++k) {
       const int s = k % STAGES;
       if (k >= STAGES && !bulk::mbar_wait(&empty[s], ((k / STAGES) - 1) & 1)) {
-        atomicOr(A.err, kErrTimeout);
+        LBM_ATOMIC_OR(A.err, (int)kErrTimeout);
         ok = false;
         break;
       }
@@ -169,7 +169,10 @@ __global__ void __launch_bounds__(bulk::kThreads) k_step_bulk(const BulkArgs A) 
           const int sz = ez == 1 ? zm : (ez == -1 ? zp : tc.z);
           const T *src = fin + (size_t)i * a.plane + (uint32_t)sz * row + (uint32_t)sy * a.pitch + lo;
           T *dst = st + ((size_t)i * TY + r) * TXH + (lo - (tc.x0 - H));
-          bulk::bulk_copy(dst, src, (uint32_t)((hi - lo) * EB), &full[s]);
+          // a refused copy (check build) leaves the stage incomplete: the
+          // consumers' bounded wait then reports kErrTimeout
+          if (LBM_CHK(src, (uint32_t)((hi - lo) * EB), 16u, kChkRead))
+            bulk::bulk_copy(dst, src, (uint32_t)((hi - lo) * EB), &full[s]);
         });
       }
     }
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(bulk::kThreads) k_step_bulk(const BulkArgs A) 
   for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++k) {
     const int s = k % STAGES;
     if (!bulk::mbar_wait(&full[s], (k / STAGES) & 1)) {
-      atomicOr(A.err, kErrTimeout);
+      LBM_ATOMIC_OR(A.err, (int)kErrTimeout);
       return;
     }
     const bulk::TileCoord tc = bulk::tile_coord(t, A.nxs, A.nys, TY);
@@ -221,9 +224,9 @@ __global__ void __launch_bounds__(bulk::kThreads) k_step_bulk(const BulkArgs A) 
       const uint32_t dc = ((uint32_t)tc.z * a.ny + y) * a.nx + x;
       float Fx = 0.f, Fy = 0.f, Fz = 0.f;
       if constexpr (FORCE) {
-        Fx = __ldg(a.force + dc);
-        Fy = __ldg(a.force + a.cells + dc);
-        Fz = __ldg(a.force + 2 * (size_t)a.cells + dc);
+        Fx = LBM_LDG(a.force + dc);
+        Fy = LBM_LDG(a.force + a.cells + dc);
+        Fz = LBM_LDG(a.force + 2 * (size_t)a.cells + dc);
       }
       float rho, ux, uy, uz;
       collide<FORCE>(d, a.omega, a.kf, Fx, Fy, Fz, rho, ux, uy, uz);
@@ -272,6 +275,7 @@ static cudaError_t bulk_launch(const StepArgs &g, int *err, int sms, cudaStream_
 
 cudaError_t launch_step_bulk(int storage, const StepArgs &a, int *err, int variant, int sms,
                              cudaStream_t s) {
+  LBM_CHECK_TABLE(s, LBM_STEP_RANGES(a, elem_bytes_of(storage)), chk_rw(err, sizeof(int)));
   switch (storage) {
     case kF32:
       return variant == 1 ? bulk_launch<0, 1, 6>(a, err, sms, s) : bulk_launch<0, 2, 3>(a, err, sms, s);

@@ -121,13 +121,13 @@ __global__ void LBM_X2_BOUNDS k_step_x2(const StepArgs a) {
   const uint32_t dc = ((uint32_t)z * a.ny + y) * a.nx + x0;
   float F0x = 0.f, F0y = 0.f, F0z = 0.f, F1x = 0.f, F1y = 0.f, F1z = 0.f;
   if constexpr (FORCE) {
-    F0x = __ldg(a.force + dc);
-    F0y = __ldg(a.force + a.cells + dc);
-    F0z = __ldg(a.force + 2 * (size_t)a.cells + dc);
+    F0x = LBM_LDG(a.force + dc);
+    F0y = LBM_LDG(a.force + a.cells + dc);
+    F0z = LBM_LDG(a.force + 2 * (size_t)a.cells + dc);
     if (has1) {
-      F1x = __ldg(a.force + dc + 1);
-      F1y = __ldg(a.force + a.cells + dc + 1);
-      F1z = __ldg(a.force + 2 * (size_t)a.cells + dc + 1);
+      F1x = LBM_LDG(a.force + dc + 1);
+      F1y = LBM_LDG(a.force + a.cells + dc + 1);
+      F1z = LBM_LDG(a.force + 2 * (size_t)a.cells + dc + 1);
     }
   }
   if constexpr (W == 3) {
@@ -142,15 +142,15 @@ __global__ void LBM_X2_BOUNDS k_step_x2(const StepArgs a) {
     Pack16<S>::store(fout + (size_t)i * a.plane + n0.c, d0[i], d1[i]);
   });
   if constexpr (MOM) {
-    a.rho[dc] = r0;
-    a.u[dc] = u0x;
-    a.u[a.cells + dc] = u0y;
-    a.u[2 * (size_t)a.cells + dc] = u0z;
+    LBM_ST(&a.rho[dc], r0);
+    LBM_ST(&a.u[dc], u0x);
+    LBM_ST(&a.u[a.cells + dc], u0y);
+    LBM_ST(&a.u[2 * (size_t)a.cells + dc], u0z);
     if (has1) {
-      a.rho[dc + 1] = r1;
-      a.u[dc + 1] = u1x;
-      a.u[a.cells + dc + 1] = u1y;
-      a.u[2 * (size_t)a.cells + dc + 1] = u1z;
+      LBM_ST(&a.rho[dc + 1], r1);
+      LBM_ST(&a.u[dc + 1], u1x);
+      LBM_ST(&a.u[a.cells + dc + 1], u1y);
+      LBM_ST(&a.u[2 * (size_t)a.cells + dc + 1], u1z);
     }
   }
 }
@@ -187,6 +187,7 @@ cudaError_t launch_step_x2(int storage, bool moments, const StepArgs &a, int bxp
                            cudaStream_t s) {
   const int pairs = (a.nx + 1) / 2;
   const dim3 g((pairs + bxp - 1) / bxp, (a.ny + by - 1) / by, a.zn), b(bxp, by, 1);
+  LBM_CHECK_TABLE(s, LBM_STEP_RANGES(a, elem_bytes_of(storage)));
   switch (storage) {
     case kF32: x2_dispatch<0>(moments, a, g, b, s); break;
     case kF16: x2_dispatch<1>(moments, a, g, b, s); break;

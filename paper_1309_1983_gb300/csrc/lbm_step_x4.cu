@@ -176,14 +176,14 @@ __device__ __forceinline__ void x4_group(const StepArgs &a, const Group &g, int 
     float F0x = 0.f, F0y = 0.f, F0z = 0.f, F1x = 0.f, F1y = 0.f, F1z = 0.f;
     if constexpr (FORCE) {
       if (has0) {
-        F0x = __ldg(a.force + dc0 + k0);
-        F0y = __ldg(a.force + a.cells + dc0 + k0);
-        F0z = __ldg(a.force + 2 * (size_t)a.cells + dc0 + k0);
+        F0x = LBM_LDG(a.force + dc0 + k0);
+        F0y = LBM_LDG(a.force + a.cells + dc0 + k0);
+        F0z = LBM_LDG(a.force + 2 * (size_t)a.cells + dc0 + k0);
       }
       if (has1) {
-        F1x = __ldg(a.force + dc0 + k1);
-        F1y = __ldg(a.force + a.cells + dc0 + k1);
-        F1z = __ldg(a.force + 2 * (size_t)a.cells + dc0 + k1);
+        F1x = LBM_LDG(a.force + dc0 + k1);
+        F1y = LBM_LDG(a.force + a.cells + dc0 + k1);
+        F1z = LBM_LDG(a.force + 2 * (size_t)a.cells + dc0 + k1);
       }
     }
     float r0, u0x, u0y, u0z, r1, u1x, u1y, u1z;
@@ -195,16 +195,16 @@ __device__ __forceinline__ void x4_group(const StepArgs &a, const Group &g, int 
     });
     if constexpr (MOM) {
       if (has0) {
-        a.rho[dc0 + k0] = r0;
-        a.u[dc0 + k0] = u0x;
-        a.u[a.cells + dc0 + k0] = u0y;
-        a.u[2 * (size_t)a.cells + dc0 + k0] = u0z;
+        LBM_ST(&a.rho[dc0 + k0], r0);
+        LBM_ST(&a.u[dc0 + k0], u0x);
+        LBM_ST(&a.u[a.cells + dc0 + k0], u0y);
+        LBM_ST(&a.u[2 * (size_t)a.cells + dc0 + k0], u0z);
       }
       if (has1) {
-        a.rho[dc0 + k1] = r1;
-        a.u[dc0 + k1] = u1x;
-        a.u[a.cells + dc0 + k1] = u1y;
-        a.u[2 * (size_t)a.cells + dc0 + k1] = u1z;
+        LBM_ST(&a.rho[dc0 + k1], r1);
+        LBM_ST(&a.u[dc0 + k1], u1x);
+        LBM_ST(&a.u[a.cells + dc0 + k1], u1y);
+        LBM_ST(&a.u[2 * (size_t)a.cells + dc0 + k1], u1z);
       }
     }
   });
@@ -264,6 +264,7 @@ cudaError_t launch_step_x4(int storage, bool moments, const StepArgs &a, int bxq
                            cudaStream_t s) {
   const int groups = (a.nx + 3) / 4;
   const dim3 g((groups + bxq - 1) / bxq, (a.ny + by - 1) / by, a.zn), b(bxq, by, 1);
+  LBM_CHECK_TABLE(s, LBM_STEP_RANGES(a, elem_bytes_of(storage)));
   switch (storage) {
     case kF16: x4_dispatch<1>(moments, a, g, b, s); break;
     case kBF16: x4_dispatch<2>(moments, a, g, b, s); break;

@@ -7,6 +7,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "check.cuh"
+
 namespace lbm {
 
 // Loads and stores of an aligned pair of values, as two floats.
@@ -16,20 +18,20 @@ struct Pack16;
 template <>
 struct Pack16<0> {
   static __device__ __forceinline__ float2 load(const float *p) {
-    return __ldg(reinterpret_cast<const float2 *>(p));
+    return LBM_LDG(reinterpret_cast<const float2 *>(p));
   }
   static __device__ __forceinline__ void store(float *p, float lo, float hi) {
-    __stcs(reinterpret_cast<float2 *>(p), make_float2(lo, hi));
+    LBM_STCS(reinterpret_cast<float2 *>(p), make_float2(lo, hi));
   }
 };
 
 template <>
 struct Pack16<1> {
   static __device__ __forceinline__ float2 load(const __half *p) {
-    return unpack(__ldg(reinterpret_cast<const unsigned int *>(p)));
+    return unpack(LBM_LDG(reinterpret_cast<const unsigned int *>(p)));
   }
   static __device__ __forceinline__ void store(__half *p, float lo, float hi) {
-    __stcs(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
+    LBM_STCS(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
   }
   static __device__ __forceinline__ float2 unpack(uint32_t v) {
     return __half22float2(*reinterpret_cast<const __half2 *>(&v));
@@ -43,10 +45,10 @@ struct Pack16<1> {
 template <>
 struct Pack16<2> {
   static __device__ __forceinline__ float2 load(const __nv_bfloat16 *p) {
-    return unpack(__ldg(reinterpret_cast<const unsigned int *>(p)));
+    return unpack(LBM_LDG(reinterpret_cast<const unsigned int *>(p)));
   }
   static __device__ __forceinline__ void store(__nv_bfloat16 *p, float lo, float hi) {
-    __stcs(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
+    LBM_STCS(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
   }
   static __device__ __forceinline__ float2 unpack(uint32_t v) {
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v));
@@ -68,7 +70,7 @@ struct Quad16 {
   using V = uint2;
   template <class T>
   static __device__ __forceinline__ V load(const T *p) {
-    return __ldg(reinterpret_cast<const uint2 *>(p));
+    return LBM_LDG(reinterpret_cast<const uint2 *>(p));
   }
   template <int k>
   static __device__ __forceinline__ float get(const V &v) {

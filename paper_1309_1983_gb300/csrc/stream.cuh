@@ -171,9 +171,9 @@ __device__ __forceinline__ void step_node(
   const uint32_t dc = ((uint32_t)z * ny + y) * nx + x;
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
   if constexpr (FORCE) {
-    Fx = __ldg(force + dc);
-    Fy = __ldg(force + cells + dc);
-    Fz = __ldg(force + 2 * (size_t)cells + dc);
+    Fx = LBM_LDG(force + dc);
+    Fy = LBM_LDG(force + cells + dc);
+    Fz = LBM_LDG(force + 2 * (size_t)cells + dc);
   }
   float rho, ux, uy, uz;
   collide<FORCE>(d, omega, kf, Fx, Fy, Fz, rho, ux, uy, uz);
@@ -182,10 +182,10 @@ __device__ __forceinline__ void step_node(
     Store<S>::st(fout + (size_t)i * plane + n.c, d[i]);
   });
   if constexpr (MOM) {
-    rho_out[dc] = rho;
-    u_out[dc] = ux;
-    u_out[cells + dc] = uy;
-    u_out[2 * (size_t)cells + dc] = uz;
+    LBM_ST(&rho_out[dc], rho);
+    LBM_ST(&u_out[dc], ux);
+    LBM_ST(&u_out[cells + dc], uy);
+    LBM_ST(&u_out[2 * (size_t)cells + dc], uz);
   }
 }
 

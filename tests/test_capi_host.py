@@ -29,7 +29,7 @@ def test_binding_covers_every_declared_symbol():
 
 
 def test_strerror_names_every_code(lib):
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):
         s = capi.strerror(code)
         assert s.startswith("LBM_"), s
     assert "unknown" in capi.strerror(-99)
@@ -234,3 +234,21 @@ def test_four_node_kernel_needs_sixteen_bit_storage_and_halfway_walls(lib):
         assert lib.lbm_set_kernel(h, capi.LBM_KERNEL_X4) == capi.LBM_EINVAL
     finally:
         lib.lbm_destroy(h)
+
+
+def test_check_calls_are_not_in_the_normal_build(lib):
+    # the checked debug build is liblbm_check.so; the normal one says so
+    assert lib.lbm_check_reset() == capi.LBM_ENOTSUP
+    assert lib.lbm_check_narrow(0) == capi.LBM_ENOTSUP
+    with pytest.raises(capi.LBMError) as e:
+        capi.check_status()
+    assert e.value.code == capi.LBM_ENOTSUP
+
+
+def test_check_build_compiles_and_exports_every_symbol():
+    path = B.build(check=True)
+    assert path.endswith("liblbm_check.so")
+    chk = ctypes.CDLL(path)
+    missing = [n for n in capi.header_symbols() if not hasattr(chk, n)]
+    assert not missing, missing
+
