@@ -6,7 +6,8 @@ at a few GB of device memory so that a full ``ncu`` capture, which saves and
 restores device memory around its passes, ends in about a minute.
 
     python -m paper_1309_1983_gb300.profile_cases step --geometry cavity --storage f16 --n 256
-        init + 4 plain step launches (k_step_x2 by default; --kernel x4 / node)
+        init + 4 plain step launches (k_step_x2 by default; --kernel x4 / node;
+        --onsite: on-site velocity walls instead of halfway bounce-back)
     python -m paper_1309_1983_gb300.profile_cases batch-adjoint --steps 4
         the 64-cavity batch: one forward sequence with moments, then two
         reverse-sequence launches (k_batch_adj_seq) of `steps` steps each
@@ -20,12 +21,12 @@ import sys
 
 
 def step(geometry: str = "cavity", storage: str = "f16", n: int = 256, launches: int = 4,
-         tau: float = 0.55, kernel: str = "x2") -> None:
+         tau: float = 0.55, kernel: str = "x2", onsite: bool = False) -> None:
     import torch
     from .lattice import Lattice
     walls = (geometry == "cavity",) * 3
     L = Lattice(n, n, n, tau, walls=walls, lid=(0.05, 0.0, 0.0) if geometry == "cavity" else None,
-                storage=storage)
+                storage=storage, onsite=onsite)
     L.set_graph_steps(0)
     L.set_kernel(kernel)
     L.init_equilibrium()
@@ -73,12 +74,14 @@ def main(argv=None) -> int:
     s.add_argument("--n", type=int, default=256)
     s.add_argument("--launches", type=int, default=4)
     s.add_argument("--kernel", default="x2", choices=["x2", "x4", "node"])
+    s.add_argument("--onsite", action="store_true")
+    s.add_argument("--tau", type=float, default=0.55)
     b = sub.add_parser("batch-adjoint")
     b.add_argument("--steps", type=int, default=4)
     b.add_argument("--launches", type=int, default=2)
     a = p.parse_args(argv)
     if a.case == "step":
-        step(a.geometry, a.storage, a.n, a.launches, kernel=a.kernel)
+        step(a.geometry, a.storage, a.n, a.launches, tau=a.tau, kernel=a.kernel, onsite=a.onsite)
     else:
         batch_adjoint(a.steps, a.launches)
     print("ok")
