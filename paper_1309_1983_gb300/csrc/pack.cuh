@@ -1,6 +1,7 @@
 // pack.cuh - aligned multi-value loads and stores of one distribution
 // plane, converted to and from FP32: pairs (x0, x0 + 1) for the two-node
 // step kernel and groups of four (x0 .. x0 + 3) for the four-node kernel.
+// 16-bit loads carry the 256-byte L2 prefetch hint (d3q19.cuh).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -8,6 +9,7 @@
 #include <stdint.h>
 
 #include "check.cuh"
+#include "d3q19.cuh"
 
 namespace lbm {
 
@@ -28,7 +30,7 @@ struct Pack16<0> {
 template <>
 struct Pack16<1> {
   static __device__ __forceinline__ float2 load(const __half *p) {
-    return unpack(LBM_LDG(reinterpret_cast<const unsigned int *>(p)));
+    return unpack(ld_nc_pf256_b32(p));
   }
   static __device__ __forceinline__ void store(__half *p, float lo, float hi) {
     LBM_STCS(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
@@ -45,7 +47,7 @@ struct Pack16<1> {
 template <>
 struct Pack16<2> {
   static __device__ __forceinline__ float2 load(const __nv_bfloat16 *p) {
-    return unpack(LBM_LDG(reinterpret_cast<const unsigned int *>(p)));
+    return unpack(ld_nc_pf256_b32(p));
   }
   static __device__ __forceinline__ void store(__nv_bfloat16 *p, float lo, float hi) {
     LBM_STCS(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
@@ -70,7 +72,7 @@ struct Quad16 {
   using V = uint2;
   template <class T>
   static __device__ __forceinline__ V load(const T *p) {
-    return LBM_LDG(reinterpret_cast<const uint2 *>(p));
+    return ld_nc_pf256_v2b32(p);
   }
   template <int k>
   static __device__ __forceinline__ float get(const V &v) {
