@@ -83,7 +83,8 @@ def measured_hbm():
 def kernel_source_hash():
     h = hashlib.sha256()
     for rel in ("paper_1309_1983_gb300/csrc/lbm_step_x2.cu", "paper_1309_1983_gb300/csrc/d3q19.cuh",
-                "paper_1309_1983_gb300/csrc/stream.cuh", "paper_1309_1983_gb300/csrc/internal.h"):
+                "paper_1309_1983_gb300/csrc/stream.cuh", "paper_1309_1983_gb300/csrc/internal.h",
+                "paper_1309_1983_gb300/csrc/pack.cuh", "paper_1309_1983_gb300/csrc/check.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

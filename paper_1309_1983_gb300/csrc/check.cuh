@@ -127,9 +127,45 @@ static inline cudaError_t check_table(cudaStream_t s, std::initializer_list<Chec
 
 #endif
 
+// ---- L2 prefetch-hinted loads -------------------------------------------------
+// Read-only (non-coherent) and L2-only loads that also ask L2 for the whole
+// 256-byte block around the address (the .L2::256B prefetch-size
+// qualifier). The kernels stream every plane row by row: a warp's loads span
+// 64 to 256 bytes, and the hint fetches the block the next warps of the row
+// will read in the same request. Measured on GB300: +1.7% for the 16-bit
+// step at 384^3 (pair loads of 128 bytes per warp; the 128-byte hint changes
+// nothing), +0.6 to 1.4% for the one-node FP32 kernels (batched forward and
+// reverse sequences, adjoint step), no change for the FP32 two-node step
+// (its pair loads already span 256 bytes). DRAM bytes and instruction counts
+// are unchanged. Types other than the ones below use the plain intrinsics.
+__device__ __forceinline__ float ldg_pf(const float *p) {
+  float v;
+  asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float2 ldg_pf(const float2 *p) {
+  float2 v;
+  asm("ld.global.nc.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+template <class T>
+__device__ __forceinline__ T ldg_pf(const T *p) {
+  return __ldg(p);
+}
+__device__ __forceinline__ float ldcg_pf(const float *p) {
+  float v;
+  asm("ld.global.cg.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+template <class T>
+__device__ __forceinline__ T ldcg_pf(const T *p) {
+  return __ldcg(p);
+}
+
 // ---- accessors ---------------------------------------------------------------
 // LBM_LD: plain load; LBM_LDV: volatile load; LBM_LDG: read-only
-// (non-coherent) path; LBM_LDCG: L2 only; LBM_ST: plain store (*p = v);
+// (non-coherent) path; LBM_LDCG: L2 only (both with the prefetch hint
+// above where the type has one); LBM_ST: plain store (*p = v);
 // LBM_ACC: plain *p += v; LBM_STCS: streaming store; LBM_ATOMIC_ADD,
 // LBM_ATOMIC_OR: atomicAdd, atomicOr; LBM_VALID(p): whether the whole object
 // at p may be read (for structures read field by field through a reference).
@@ -148,11 +184,11 @@ __device__ __forceinline__ T chk_ldv(const T *p) {
 }
 template <class T>
 __device__ __forceinline__ T chk_ldg(const T *p) {
-  return LBM_CHK(p, sizeof(T), sizeof(T), kChkRead) ? __ldg(p) : T{};
+  return LBM_CHK(p, sizeof(T), sizeof(T), kChkRead) ? ldg_pf(p) : T{};
 }
 template <class T>
 __device__ __forceinline__ T chk_ldcg(const T *p) {
-  return LBM_CHK(p, sizeof(T), sizeof(T), kChkRead) ? __ldcg(p) : T{};
+  return LBM_CHK(p, sizeof(T), sizeof(T), kChkRead) ? ldcg_pf(p) : T{};
 }
 template <class T, class U>
 __device__ __forceinline__ void chk_st(T *p, U v) {
@@ -191,8 +227,8 @@ __device__ __forceinline__ bool chk_valid(const T *p) {
 #else
 #define LBM_LD(p) (*(p))
 #define LBM_LDV(p) (*(const volatile decltype(+*(p)) *)(p))
-#define LBM_LDG(p) __ldg(p)
-#define LBM_LDCG(p) __ldcg(p)
+#define LBM_LDG(p) ::lbm::ldg_pf(p)
+#define LBM_LDCG(p) ::lbm::ldcg_pf(p)
 #define LBM_ST(p, v) ((void)(*(p) = (v)))
 #define LBM_ACC(p, v) ((void)(*(p) += (v)))
 #define LBM_STCS(p, v) __stcs((p), (v))
@@ -200,5 +236,26 @@ __device__ __forceinline__ bool chk_valid(const T *p) {
 #define LBM_ATOMIC_OR(p, v) atomicOr((p), (v))
 #define LBM_VALID(p) true
 #endif
+
+// 16-, 32- and 64-bit raw loads of 16-bit storage (pairs and groups of four
+// values), with the prefetch hint, checked like every access.
+__device__ __forceinline__ unsigned short ldg_pf_b16(const void *p) {
+  if (!LBM_CHK(p, 2u, 2u, kChkRead)) return 0;
+  unsigned short v;
+  asm("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned ldg_pf_b32(const void *p) {
+  if (!LBM_CHK(p, 4u, 4u, kChkRead)) return 0u;
+  unsigned v;
+  asm("ld.global.nc.L2::256B.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ldg_pf_v2b32(const void *p) {
+  if (!LBM_CHK(p, 8u, 8u, kChkRead)) return make_uint2(0u, 0u);
+  uint2 v;
+  asm("ld.global.nc.L2::256B.v2.b32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
 
 }  // namespace lbm

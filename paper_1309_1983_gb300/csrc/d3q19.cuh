@@ -52,32 +52,6 @@ __device__ __forceinline__ void static_for(F &&f) {
 // ld(): read-only path (ld.global.nc), valid when the buffer is not written
 // during the kernel. ld_l2(): L2-only path (ld.global.cg) for persistent
 // kernels in which other blocks rewrite the buffer between grid barriers.
-// Read-only 16- and 32-bit loads that also ask L2 for the whole 256-byte
-// block around the address (the .L2::256B prefetch-size qualifier). A warp's
-// 16-bit loads span 64 or 128 bytes; the prefetch brings in the bytes the
-// next warps of the row will read, with one request. Measured on GB300 at
-// 384^3: +1.7% for the 16-bit step (cavity and periodic); the 128-byte hint
-// changes nothing, and FP32 pair loads already span 256 bytes per warp, so
-// FP32 keeps plain __ldg. Checked like every other access in LBM_CHECK builds.
-__device__ __forceinline__ unsigned short ld_nc_pf256_b16(const void *p) {
-  if (!LBM_CHK(p, 2u, 2u, kChkRead)) return 0;
-  unsigned short v;
-  asm("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ unsigned ld_nc_pf256_b32(const void *p) {
-  if (!LBM_CHK(p, 4u, 4u, kChkRead)) return 0u;
-  unsigned v;
-  asm("ld.global.nc.L2::256B.b32 %0, [%1];" : "=r"(v) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ uint2 ld_nc_pf256_v2b32(const void *p) {
-  if (!LBM_CHK(p, 8u, 8u, kChkRead)) return make_uint2(0u, 0u);
-  uint2 v;
-  asm("ld.global.nc.L2::256B.v2.b32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
-  return v;
-}
-
 template <int S>
 struct Store;
 
@@ -93,7 +67,7 @@ template <>
 struct Store<1> {
   using T = __half;
   static __device__ __forceinline__ float ld(const T *p) {
-    return __half2float(__ushort_as_half(ld_nc_pf256_b16(p)));
+    return __half2float(__ushort_as_half(ldg_pf_b16(p)));
   }
   static __device__ __forceinline__ float ld_l2(const T *p) {
     return __half2float(LBM_LDCG(p));
@@ -107,7 +81,7 @@ template <>
 struct Store<2> {
   using T = __nv_bfloat16;
   static __device__ __forceinline__ float ld(const T *p) {
-    return __bfloat162float(__ushort_as_bfloat16(ld_nc_pf256_b16(p)));
+    return __bfloat162float(__ushort_as_bfloat16(ldg_pf_b16(p)));
   }
   static __device__ __forceinline__ float ld_l2(const T *p) {
     return __bfloat162float(LBM_LDCG(p));

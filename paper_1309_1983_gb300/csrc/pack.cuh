@@ -1,7 +1,7 @@
 // pack.cuh - aligned multi-value loads and stores of one distribution
 // plane, converted to and from FP32: pairs (x0, x0 + 1) for the two-node
 // step kernel and groups of four (x0 .. x0 + 3) for the four-node kernel.
-// 16-bit loads carry the 256-byte L2 prefetch hint (d3q19.cuh).
+// Loads carry the 256-byte L2 prefetch hint (check.cuh).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -9,7 +9,6 @@
 #include <stdint.h>
 
 #include "check.cuh"
-#include "d3q19.cuh"
 
 namespace lbm {
 
@@ -30,7 +29,7 @@ struct Pack16<0> {
 template <>
 struct Pack16<1> {
   static __device__ __forceinline__ float2 load(const __half *p) {
-    return unpack(ld_nc_pf256_b32(p));
+    return unpack(ldg_pf_b32(p));
   }
   static __device__ __forceinline__ void store(__half *p, float lo, float hi) {
     LBM_STCS(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
@@ -47,7 +46,7 @@ struct Pack16<1> {
 template <>
 struct Pack16<2> {
   static __device__ __forceinline__ float2 load(const __nv_bfloat16 *p) {
-    return unpack(ld_nc_pf256_b32(p));
+    return unpack(ldg_pf_b32(p));
   }
   static __device__ __forceinline__ void store(__nv_bfloat16 *p, float lo, float hi) {
     LBM_STCS(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
@@ -72,7 +71,7 @@ struct Quad16 {
   using V = uint2;
   template <class T>
   static __device__ __forceinline__ V load(const T *p) {
-    return ld_nc_pf256_v2b32(p);
+    return ldg_pf_v2b32(p);
   }
   template <int k>
   static __device__ __forceinline__ float get(const V &v) {
