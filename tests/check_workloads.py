@@ -13,7 +13,11 @@ test named by LBM_LIBRARY:
 --narrow B ends every range of every launch table B bytes early
 (lbm_check_narrow) for one plain step of a periodic FP32 lattice, and
 records the first refused access and the tails of the buffers it could lie
-in. Inputs are seeded; nothing here is compared with the oracle (the parity
+in. --large runs the benchmark's sizes instead (one step of 384^3 periodic
+FP32, 384^3 cavity FP16 with halfway and with on-site walls, the 1024^3
+FP32 cavity (163 GB of f), and the 64-cavity batch: persistent steps, a
+step sequence with moments and a reverse sequence) and records only the
+refusals. Inputs are seeded; nothing here is compared with the oracle (the parity
 tests do that for the normal build).
 """
 
@@ -263,11 +267,61 @@ def narrow(nbytes):
         L.close()
 
 
+def large():
+    from paper_1309_1983_gb300 import workloads as W
+    res = {}
+
+    def one(name, n, geom, storage, onsite=False):
+        walls = (geom == "cavity",) * 3
+        L = Lattice(n, n, n, 0.6, walls=walls, lid=(0.05, 0.0, 0.0) if walls[0] else None,
+                    storage=storage, onsite=onsite)
+        try:
+            L.set_graph_steps(0)
+            L.init_equilibrium()
+            L.step(1)
+            m = L.mass()
+            res[name] = {"refused": refused(), "mass": m}
+        finally:
+            L.close()
+            torch.cuda.empty_cache()
+
+    one("periodic_384_f32", 384, "periodic", "f32")
+    one("cavity_384_f16", 384, "cavity", "f16")
+    one("onsite_384_f16", 384, "cavity", "f16", onsite=True)
+    one("cavity_1024_f32", 1024, "cavity", "f32")
+    G = W.batch_geometry(64, seed=3)
+    B = Batch(G.dims, G.tau, G.lid_u)
+    try:
+        B.init_rest()
+        B.step(4)
+        f0, f1 = B.current_buffers()
+        k = 8
+        rho = [torch.empty(B.cells, device="cuda") for _ in range(k)]
+        u = [torch.empty(3 * B.cells, device="cuda") for _ in range(k)]
+        ptrs = BatchAdjointProblem._ptrs
+        fins = [f0 if j % 2 == 0 else f1 for j in range(k)]
+        fouts = [f1 if j % 2 == 0 else f0 for j in range(k)]
+        capi.call("lbm_batch_run", B.handle, k, ptrs(fins), ptrs(fouts), ptrs(rho), ptrs(u))
+        lam = [torch.full((B.f_bytes // 4,), 1e-3, device="cuda") for _ in range(2)]
+        gF = torch.zeros(3 * B.cells, device="cuda")
+        capi.call("lbm_batch_adjoint_run", B.handle, k, ptrs(rho[::-1]), ptrs(u[::-1]),
+                  capi._vp(lam[0].data_ptr()), capi._vp(lam[1].data_ptr()),
+                  capi._vp(gF.data_ptr()))
+        res["batch_64_cavities"] = {"refused": refused(), "cells": int(B.cells)}
+    finally:
+        B.close()
+    return res
+
+
 def main(argv):
     out_path = argv[0]
     res = {"library": os.path.basename(capi.LIB_PATH), "checked": CHECKED}
     if "--narrow" in argv:
         res["narrow"] = narrow(int(argv[argv.index("--narrow") + 1]))
+    elif "--large" in argv:
+        if CHECKED:
+            refused()
+        res["large"] = large()
     else:
         capi.load()
         if CHECKED:

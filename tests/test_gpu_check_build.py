@@ -13,6 +13,10 @@ process of its own. The tests check that
 * the checked build refuses no access in any workload;
 * both builds give the same bits for every output (the checks change no
   arithmetic), so what was checked is what the normal build computes;
+* at the benchmark's sizes (384^3 steps in FP32 and FP16, halfway and
+  on-site walls, the 1024^3 FP32 cavity, the 64-cavity batch with its
+  persistent, sequence and reverse-sequence kernels) no access is refused
+  either;
 * with every table range ended 64 bytes early (lbm_check_narrow) a plain
   step's accesses to those tails are refused and the first one is reported
   with its address inside one of the two f buffers' tails: refusals are
@@ -84,3 +88,13 @@ def test_narrowed_tables_are_refused_and_reported(libs, tmp_path):
     assert res["refused"] > 0, res
     assert any(lo <= res["first"] < hi for lo, hi in res["tails"]), res
     assert res["bytes"] in (4, 8) and res["kind"] in (1, 2), res
+
+
+def test_checked_build_refuses_no_access_at_full_size(libs, tmp_path):
+    import torch
+    torch.cuda.empty_cache()  # the child needs 163 GB for the 1024^3 lattice
+    res = _run(tmp_path / "large.json", libs[1], "--large")["large"]
+    assert set(res) == {"periodic_384_f32", "cavity_384_f16", "onsite_384_f16",
+                        "cavity_1024_f32", "batch_64_cavities"}, res
+    bad = {k: v["refused"] for k, v in res.items() if v["refused"]}
+    assert not bad, bad
