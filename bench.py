@@ -225,6 +225,10 @@ def run_reference(args):
               f"workload; same per-node arithmetic)")
     # the config names the lattice actually timed, and the workload it samples
     config = dict(workload_config(n), sample_of=workload_config(args.n)["workload"])
+    # the oracle keeps plain FP64 f in host memory (array of structures)
+    config["storage"] = "f64 f_i (oracle, array of structures)"
+    config["l2"] = (f"host run: {2 * 19 * 8 * n ** 3 / 1e9:.2f} GB of FP64 state in host memory "
+                    "(no GPU cache involved)")
     line = {
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
