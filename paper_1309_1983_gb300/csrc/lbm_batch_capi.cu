@@ -110,7 +110,7 @@ bool aligned_to(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 constexpr size_t kMaxSeqGraphs = 512;
 
 // One cooperative launch through `launch(stream)` (barrier words reset
-// first), replayed from a CUDA graph cached under `key` when the driver can
+// first), replayed from a CUDA graph cached under `key` when CUDA can
 // capture it; waits for the launch and reports a barrier timeout.
 template <class Launch>
 int coop_run(lbm_batch *b,
