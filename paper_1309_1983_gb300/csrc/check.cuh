@@ -166,7 +166,7 @@ __device__ __forceinline__ T ldcg_pf(const T *p) {
 // LBM_LD: plain load; LBM_LDV: volatile load; LBM_LDG: read-only
 // (non-coherent) path; LBM_LDCG: L2 only (both with the prefetch hint
 // above where the type has one); LBM_ST: plain store (*p = v);
-// LBM_ACC: plain *p += v; LBM_STCS: streaming store; LBM_ATOMIC_ADD,
+// LBM_ACC: plain *p += v; LBM_ATOMIC_ADD,
 // LBM_ATOMIC_OR: atomicAdd, atomicOr; LBM_VALID(p): whether the whole object
 // at p may be read (for structures read field by field through a reference).
 // In the normal build each is the bare expression it names, textually, so
@@ -199,10 +199,6 @@ __device__ __forceinline__ void chk_acc(T *p, U v) {
   if (LBM_CHK(p, sizeof(T), sizeof(T), kChkRW)) *p += v;
 }
 template <class T>
-__device__ __forceinline__ void chk_stcs(T *p, T v) {
-  if (LBM_CHK(p, sizeof(T), sizeof(T), kChkWrite)) __stcs(p, v);
-}
-template <class T>
 __device__ __forceinline__ T chk_atomic_add(T *p, T v) {
   return LBM_CHK(p, sizeof(T), sizeof(T), kChkRW) ? atomicAdd(p, v) : T{};
 }
@@ -220,7 +216,6 @@ __device__ __forceinline__ bool chk_valid(const T *p) {
 #define LBM_LDCG(p) ::lbm::chk_ldcg(p)
 #define LBM_ST(p, v) ::lbm::chk_st((p), (v))
 #define LBM_ACC(p, v) ::lbm::chk_acc((p), (v))
-#define LBM_STCS(p, v) ::lbm::chk_stcs((p), (v))
 #define LBM_ATOMIC_ADD(p, v) ::lbm::chk_atomic_add((p), (v))
 #define LBM_ATOMIC_OR(p, v) ::lbm::chk_atomic_or((p), (v))
 #define LBM_VALID(p) ::lbm::chk_valid(p)
@@ -231,7 +226,6 @@ __device__ __forceinline__ bool chk_valid(const T *p) {
 #define LBM_LDCG(p) ::lbm::ldcg_pf(p)
 #define LBM_ST(p, v) ((void)(*(p) = (v)))
 #define LBM_ACC(p, v) ((void)(*(p) += (v)))
-#define LBM_STCS(p, v) __stcs((p), (v))
 #define LBM_ATOMIC_ADD(p, v) atomicAdd((p), (v))
 #define LBM_ATOMIC_OR(p, v) atomicOr((p), (v))
 #define LBM_VALID(p) true

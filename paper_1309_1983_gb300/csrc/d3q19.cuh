@@ -61,7 +61,7 @@ struct Store<0> {
   static __device__ __forceinline__ float ld(const T *p) { return LBM_LDG(p); }
   static __device__ __forceinline__ float ld_l2(const T *p) { return LBM_LDCG(p); }
   static __device__ __forceinline__ float ld_smem(const T *p) { return *p; }
-  static __device__ __forceinline__ void st(T *p, float v) { LBM_STCS(p, v); }
+  static __device__ __forceinline__ void st(T *p, float v) { LBM_ST(p, v); }
 };
 template <>
 struct Store<1> {
@@ -74,7 +74,7 @@ struct Store<1> {
   }
   static __device__ __forceinline__ float ld_smem(const T *p) { return __half2float(*p); }
   static __device__ __forceinline__ void st(T *p, float v) {
-    LBM_STCS(p, __float2half_rn(v));
+    LBM_ST(p, __float2half_rn(v));
   }
 };
 template <>
@@ -88,7 +88,7 @@ struct Store<2> {
   }
   static __device__ __forceinline__ float ld_smem(const T *p) { return __bfloat162float(*p); }
   static __device__ __forceinline__ void st(T *p, float v) {
-    LBM_STCS(p, __float2bfloat16_rn(v));
+    LBM_ST(p, __float2bfloat16_rn(v));
   }
 };
 

@@ -159,7 +159,7 @@ __global__ void LBM_PAIR_BOUNDS k_step_pair(const StepArgs a) {
   // the high half of the last pair of an odd-length row lands in the padding
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    LBM_STCS(reinterpret_cast<unsigned int *>(fout + (size_t)i * a.plane + n0.c - n0.xo[1] + x0),
+    LBM_ST(reinterpret_cast<unsigned int *>(fout + (size_t)i * a.plane + n0.c - n0.xo[1] + x0),
            V[i]);
   });
 }

@@ -22,7 +22,7 @@ struct Pack16<0> {
     return LBM_LDG(reinterpret_cast<const float2 *>(p));
   }
   static __device__ __forceinline__ void store(float *p, float lo, float hi) {
-    LBM_STCS(reinterpret_cast<float2 *>(p), make_float2(lo, hi));
+    LBM_ST(reinterpret_cast<float2 *>(p), make_float2(lo, hi));
   }
 };
 
@@ -32,7 +32,7 @@ struct Pack16<1> {
     return unpack(ldg_pf_b32(p));
   }
   static __device__ __forceinline__ void store(__half *p, float lo, float hi) {
-    LBM_STCS(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
+    LBM_ST(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
   }
   static __device__ __forceinline__ float2 unpack(uint32_t v) {
     return __half22float2(*reinterpret_cast<const __half2 *>(&v));
@@ -49,7 +49,7 @@ struct Pack16<2> {
     return unpack(ldg_pf_b32(p));
   }
   static __device__ __forceinline__ void store(__nv_bfloat16 *p, float lo, float hi) {
-    LBM_STCS(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
+    LBM_ST(reinterpret_cast<unsigned int *>(p), pack(lo, hi));
   }
   static __device__ __forceinline__ float2 unpack(uint32_t v) {
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v));
