@@ -80,13 +80,31 @@ def measured_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = ("paper_1309_1983_gb300/csrc/lbm_step_x2.cu", "paper_1309_1983_gb300/csrc/d3q19.cuh",
+                  "paper_1309_1983_gb300/csrc/stream.cuh", "paper_1309_1983_gb300/csrc/internal.h",
+                  "paper_1309_1983_gb300/csrc/pack.cuh", "paper_1309_1983_gb300/csrc/check.cuh")
+
+
+def code_only(text):
+    """C/C++ source without comments and blank lines (what the compiler sees
+    of the kernel, as far as the hash below is concerned)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
+def kernel_source_hash(read=None):
+    """First 16 hex digits of the sha256 of the benchmark kernel's sources,
+    comments and blank lines removed; `read(rel)` may supply the texts."""
     h = hashlib.sha256()
-    for rel in ("paper_1309_1983_gb300/csrc/lbm_step_x2.cu", "paper_1309_1983_gb300/csrc/d3q19.cuh",
-                "paper_1309_1983_gb300/csrc/stream.cuh", "paper_1309_1983_gb300/csrc/internal.h",
-                "paper_1309_1983_gb300/csrc/pack.cuh", "paper_1309_1983_gb300/csrc/check.cuh"):
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
+    for rel in KERNEL_SOURCES:
+        if read is None:
+            with open(os.path.join(ROOT, rel)) as fh:
+                text = fh.read()
+        else:
+            text = read(rel)
+        h.update(code_only(text).encode())
     return h.hexdigest()[:16]
 
 

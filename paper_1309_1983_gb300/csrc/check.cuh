@@ -2,8 +2,9 @@
 // debug build behind them (a stand-in for a device memory checker).
 //
 // Every load, store and atomic of a kernel on global memory goes through the
-// accessors below. In the normal build they are the plain operations and
-// compile to the same code as writing them out. Built with -DLBM_CHECK
+// accessors below. In the normal build each is the bare operation (the
+// read-only and L2-only loads with the prefetch hint of the next section),
+// written out by the preprocessor, so no check costs anything. Built with -DLBM_CHECK
 // (liblbm_check.so), each access is first tested against the table of
 // buffers its launch was given: byte range [lo, hi), read and/or write
 // permission, and natural alignment of the access. An access that fits no
@@ -165,10 +166,10 @@ __device__ __forceinline__ T ldcg_pf(const T *p) {
 // ---- accessors ---------------------------------------------------------------
 // LBM_LD: plain load; LBM_LDV: volatile load; LBM_LDG: read-only
 // (non-coherent) path; LBM_LDCG: L2 only (both with the prefetch hint
-// above where the type has one); LBM_ST: plain store (*p = v);
-// LBM_ACC: plain *p += v; LBM_ATOMIC_ADD,
-// LBM_ATOMIC_OR: atomicAdd, atomicOr; LBM_VALID(p): whether the whole object
-// at p may be read (for structures read field by field through a reference).
+// above where the type has one); LBM_ST: plain write-back store (*p = v);
+// LBM_ACC: plain *p += v; LBM_ATOMIC_ADD, LBM_ATOMIC_OR: atomicAdd,
+// atomicOr; LBM_VALID(p): whether the whole object at p may be read (for
+// structures read field by field through a reference).
 // In the normal build each is the bare expression it names, textually, so
 // that the kernels compile exactly as written out (forwarding stores through
 // even inlined functions changed ptxas's register allocation).
