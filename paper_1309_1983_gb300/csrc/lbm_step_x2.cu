@@ -34,32 +34,86 @@ namespace lbm {
 // Pulled values of both nodes for direction i (bounce-back by address
 // selection when SEL; the e_x = 0 pulls of the pair share y, z, hence their
 // wall decisions, so they stay one paired load).
-template <int S, bool SEL, int i>
+//
+// Two ways of forming the addresses, the same values: RAW = true (the
+// periodic kernel) adds one 64-bit index i * plane + offset to the base;
+// RAW = false (the kernels with walls) selects a 32-bit plane number and a
+// 32-bit offset in it and adds plane * number, then the offset, to the base.
+// The second form lets ptxas keep the 16-bit wall kernels at 64 registers
+// instead of 70-80 (8 resident blocks of 128 threads per SM instead of 6-7):
+// +3.6% for the FP16 cavity at 384^3 (81.8 against 79.0 GLUPS), +5.4% with
+// on-site walls; the periodic kernels keep the first form, which the second
+// slows by 0.5% (FP16), and so does the FP32 on-site kernel (0.2%).
+template <int S, bool SEL, int i, bool RAW = false>
 __device__ __forceinline__ void pull_pair(const typename Store<S>::T *__restrict__ fin,
                                           uint32_t plane, const NodeIdx &n0, const NodeIdx &n1,
                                           const float (&lidc)[Q], float &v0, float &v1) {
-  using T = typename Store<S>::T;
-  if constexpr (kEx[i] == 0) {
-    size_t idx = (size_t)i * plane + source_of<i>(n0);
-    if constexpr (SEL) {
-      if (bounces<i>(n0)) idx = (size_t)kOpp_v<i> * plane + n0.c;
+  static_assert(!(RAW && SEL), "the selecting pull uses the plane / offset form");
+  if constexpr (RAW) {
+    if constexpr (kEx[i] == 0) {
+      size_t idx = (size_t)i * plane + source_of<i>(n0);
+      const float2 p = Pack16<S>::load(fin + idx);
+      v0 = p.x;
+      v1 = p.y;
+    } else {
+      size_t i0 = (size_t)i * plane + source_of<i>(n0);
+      size_t i1 = (size_t)i * plane + source_of<i>(n1);
+      v0 = Store<S>::ld(fin + i0);
+      v1 = Store<S>::ld(fin + i1);
     }
-    const float2 p = Pack16<S>::load(fin + idx);
+  } else if constexpr (kEx[i] == 0) {
+    uint32_t pl = (uint32_t)i, off = source_of<i>(n0);
+    if constexpr (SEL) {
+      if (bounces<i>(n0)) {
+        pl = (uint32_t)kOpp_v<i>;
+        off = n0.c;
+      }
+    }
+    const float2 p = Pack16<S>::load(fin + (size_t)pl * plane + off);
     v0 = p.x;
     v1 = p.y;
   } else {
-    size_t i0 = (size_t)i * plane + source_of<i>(n0);
-    size_t i1 = (size_t)i * plane + source_of<i>(n1);
+    uint32_t p0 = (uint32_t)i, o0 = source_of<i>(n0);
+    uint32_t p1 = (uint32_t)i, o1 = source_of<i>(n1);
     if constexpr (SEL) {
-      if (bounces<i>(n0)) i0 = (size_t)kOpp_v<i> * plane + n0.c;
-      if (bounces<i>(n1)) i1 = (size_t)kOpp_v<i> * plane + n1.c;
+      if (bounces<i>(n0)) {
+        p0 = (uint32_t)kOpp_v<i>;
+        o0 = n0.c;
+      }
+      if (bounces<i>(n1)) {
+        p1 = (uint32_t)kOpp_v<i>;
+        o1 = n1.c;
+      }
     }
-    v0 = Store<S>::ld(fin + i0);
-    v1 = Store<S>::ld(fin + i1);
+    v0 = Store<S>::ld(fin + (size_t)p0 * plane + o0);
+    v1 = Store<S>::ld(fin + (size_t)p1 * plane + o1);
   }
   if constexpr (SEL && kEz[i] == -1) {  // the moving plane z = nz (z1 implies a bounce)
     v0 += n0.z1 ? lidc[i] : 0.0f;
     v1 += n1.z1 ? lidc[i] : 0.0f;
+  }
+}
+
+// Pulled values of both nodes in a warp whose only wall nodes lie on the x
+// faces: the e_x = 0 pulls cannot bounce there, an e_x = +1 pull bounces only
+// on the x = 0 node and an e_x = -1 pull only on the x = nx - 1 node (no lid
+// term: the lid is the z = nz plane).
+template <int S, int i>
+__device__ __forceinline__ void pull_pair_xwall(const typename Store<S>::T *__restrict__ fin,
+                                                uint32_t plane, const NodeIdx &n0,
+                                                const NodeIdx &n1, float &v0, float &v1) {
+  if constexpr (kEx[i] == 0) {
+    const float2 p = Pack16<S>::load(fin + (size_t)i * plane + source_of<i>(n0));
+    v0 = p.x;
+    v1 = p.y;
+  } else {
+    constexpr uint32_t io = kOpp_v<i>;
+    const bool b0 = kEx[i] == 1 ? n0.x0 : n0.x1;
+    const bool b1 = kEx[i] == 1 ? n1.x0 : n1.x1;
+    const uint32_t p0 = b0 ? io : (uint32_t)i, o0 = b0 ? n0.c : source_of<i>(n0);
+    const uint32_t p1 = b1 ? io : (uint32_t)i, o1 = b1 ? n1.c : source_of<i>(n1);
+    v0 = Store<S>::ld(fin + (size_t)p0 * plane + o0);
+    v1 = Store<S>::ld(fin + (size_t)p1 * plane + o1);
   }
 }
 
@@ -74,9 +128,11 @@ __device__ __forceinline__ void pull_pair(const typename Store<S>::T *__restrict
 #endif
 
 // W: 0 periodic, 1 walls by address selection in the warps that hold a wall
-// node (a warp vote picks the plain periodic pulls for the others: no
-// divergence, and 5-14% faster than selecting in every warp), 2 walls by the
-// wall-node branch (the one-node kernel's face fix-ups, per node of the
+// node (warp votes pick, per warp, full selection where a y or z wall node
+// is present, selection of the ten e_x != 0 pulls where only x wall nodes
+// are, and the plain pulls elsewhere: no divergence; 5-14% faster than
+// selecting in every warp, and the x-only path another 0.6-1.4%), 2 walls by
+// the wall-node branch (the one-node kernel's face fix-ups, per node of the
 // pair), 3 on-site velocity walls (plain pulls, then the rule of onsite.cuh
 // on each wall node of the pair).
 template <int S, int W, bool FORCE, bool MOM>
@@ -96,11 +152,18 @@ __global__ void LBM_X2_BOUNDS k_step_x2(const StepArgs a) {
 
   float d0[Q], d1[Q];
   if constexpr (W == 1) {
-    // the vote covers the warp's active threads (the others have returned)
-    if (__any_sync(__activemask(), on_wall(n0) || on_wall(n1))) {
+    // the votes cover the warp's active threads (the others have returned);
+    // the pair shares y and z, so n0 decides the y / z faces for both
+    const unsigned m = __activemask();
+    if (__any_sync(m, n0.y0 | n0.y1 | n0.z0 | n0.z1)) {
       static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         pull_pair<S, true, i>(fin, a.plane, n0, n1, a.lidc, d0[i], d1[i]);
+      });
+    } else if (__any_sync(m, n0.x0 | n0.x1 | n1.x1)) {
+      static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        pull_pair_xwall<S, i>(fin, a.plane, n0, n1, d0[i], d1[i]);
       });
     } else {
       static_for<0, Q>([&](auto I) {
@@ -109,9 +172,12 @@ __global__ void LBM_X2_BOUNDS k_step_x2(const StepArgs a) {
       });
     }
   } else {
+    // the periodic kernel and the FP32 on-site kernel keep the 64-bit index
+    // form (see pull_pair)
+    constexpr bool RAW = W == 0 || (W == 3 && S == 0);
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      pull_pair<S, false, i>(fin, a.plane, n0, n1, a.lidc, d0[i], d1[i]);
+      pull_pair<S, false, i, RAW>(fin, a.plane, n0, n1, a.lidc, d0[i], d1[i]);
     });
   }
   if constexpr (W == 2) {
