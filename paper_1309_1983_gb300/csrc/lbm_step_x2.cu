@@ -118,7 +118,8 @@ __device__ __forceinline__ void pull_pair_xwall(const typename Store<S>::T *__re
 }
 
 // Launch bounds: by default only the block size is fixed (64 registers for
-// the periodic 16-bit kernel, 74 for FP32, up to 80 with walls);
+// the 16-bit kernels with halfway or on-site walls and without, 72 for the
+// periodic FP32 kernel, up to 80 with walls, force or fused moments);
 // LBM_X2_MIN_BLOCKS asks for that
 // many resident 256-thread blocks per SM instead (tuning experiments).
 #ifdef LBM_X2_MIN_BLOCKS
