@@ -43,7 +43,8 @@ namespace lbm {
 // instead of 70-80 (8 resident blocks of 128 threads per SM instead of 6-7):
 // +3.6% for the FP16 cavity at 384^3 (81.8 against 79.0 GLUPS), +5.4% with
 // on-site walls; the periodic kernels keep the first form, which the second
-// slows by 0.5% (FP16), and so does the FP32 on-site kernel (0.2%).
+// slows by 0.5% (FP16), and so do the FP32 on-site kernel (0.2%) and the
+// wall-node branch form (W = 2, whose registers it raises).
 template <int S, bool SEL, int i, bool RAW = false>
 __device__ __forceinline__ void pull_pair(const typename Store<S>::T *__restrict__ fin,
                                           uint32_t plane, const NodeIdx &n0, const NodeIdx &n1,
@@ -173,9 +174,9 @@ __global__ void LBM_X2_BOUNDS k_step_x2(const StepArgs a) {
       });
     }
   } else {
-    // the periodic kernel and the FP32 on-site kernel keep the 64-bit index
-    // form (see pull_pair)
-    constexpr bool RAW = W == 0 || (W == 3 && S == 0);
+    // the periodic kernel, the wall-node branch form and the FP32 on-site
+    // kernel keep the 64-bit index form (see pull_pair)
+    constexpr bool RAW = W == 0 || W == 2 || (W == 3 && S == 0);
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
       pull_pair<S, false, i, RAW>(fin, a.plane, n0, n1, a.lidc, d0[i], d1[i]);
