@@ -47,6 +47,10 @@
  *     [3][nz][ny][nx] (component-major).
  *   - Adjoint buffers (lambda) are FP32 with the FP32 f-buffer layout (same
  *     pitch), unshifted.
+ *   - Device buffers must be aligned for the kernels' accesses: f buffers to
+ *     256 bytes, field and lambda buffers to 4 bytes, a device FP64 result
+ *     (loss) to 8 bytes. A call given a misaligned buffer returns LBM_EINVAL
+ *     before it checks anything else about the handle and launches nothing.
  */
 #ifndef LBM_H
 #define LBM_H

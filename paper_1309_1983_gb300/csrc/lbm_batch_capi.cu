@@ -213,6 +213,15 @@ int persistent_grid(lbm_batch *b, int *grid) {
   return LBM_OK;
 }
 
+// Alignment the kernels' accesses need (lbm.h conventions); NULL passes here
+// (each call judges NULL itself), and it is checked before the handle.
+constexpr size_t kAlignF = 256, kAlignField = 4, kAlignF64 = 8;
+
+#define LBM_BREQUIRE_ALIGNED(cond) \
+  do {                             \
+    if (!(cond)) return bfail(LBM_EINVAL, "misaligned device buffer"); \
+  } while (0)
+
 int check_b(const lbm_batch *b) {
   if (!b) return bfail(LBM_EINVAL, "NULL handle");
   if (!b->bound) return bfail(LBM_EUNBOUND, "no buffers bound");
@@ -487,6 +496,7 @@ int lbm_batch_step_launches(lbm_batch_t *b, int n) {
 }
 
 int lbm_batch_moments(lbm_batch_t *b, float *rho, float *u) {
+  LBM_BREQUIRE_ALIGNED(aligned_to(rho, kAlignField) && aligned_to(u, kAlignField));
   int rc = check_b(b);
   if (rc) return rc;
   BCUDA(lbm::launch_batch_moments(make_args(b), b->f[b->cur], rho, u, b->threads, b->stream),
@@ -533,6 +543,7 @@ int lbm_batch_set_f(lbm_batch_t *b, int dom, const double *host_f) {
 }
 
 int lbm_batch_init_equilibrium(lbm_batch_t *b, const float *u0) {
+  LBM_BREQUIRE_ALIGNED(aligned_to(u0, kAlignField));
   int rc = check_b(b);
   if (rc) return rc;
   BCUDA(lbm::launch_batch_init_eq(make_args(b), b->f[b->cur], u0, b->threads, b->stream),
@@ -541,6 +552,7 @@ int lbm_batch_init_equilibrium(lbm_batch_t *b, const float *u0) {
 }
 
 int lbm_batch_step_to(lbm_batch_t *b, const void *f_in, void *f_out) {
+  LBM_BREQUIRE_ALIGNED(aligned_to(f_in, kAlignF) && aligned_to(f_out, kAlignF));
   int rc = check_b(b);
   if (rc) return rc;
   if (!f_in || !f_out || f_in == f_out) return bfail(LBM_EINVAL, "bad buffers");
@@ -552,6 +564,8 @@ int lbm_batch_step_to(lbm_batch_t *b, const void *f_in, void *f_out) {
 
 int lbm_batch_step_to_moments(lbm_batch_t *b, const void *f_in, void *f_out, float *rho,
                               float *u) {
+  LBM_BREQUIRE_ALIGNED(aligned_to(f_in, kAlignF) && aligned_to(f_out, kAlignF) &&
+                       aligned_to(rho, kAlignField) && aligned_to(u, kAlignField));
   int rc = check_b(b);
   if (rc) return rc;
   if (!f_in || !f_out || f_in == f_out || !rho || !u) return bfail(LBM_EINVAL, "bad buffers");
@@ -563,6 +577,9 @@ int lbm_batch_step_to_moments(lbm_batch_t *b, const void *f_in, void *f_out, flo
 
 int lbm_batch_adjoint_seed(lbm_batch_t *b, const void *f_T, const float *u_target,
                            float *lambda_T, float *grad_force, double *loss) {
+  LBM_BREQUIRE_ALIGNED(aligned_to(f_T, kAlignF) && aligned_to(u_target, kAlignField) &&
+                       aligned_to(lambda_T, kAlignField) && aligned_to(grad_force, kAlignField) &&
+                       aligned_to(loss, kAlignF64));
   int rc = check_b(b);
   if (rc) return rc;
   if (!f_T || !u_target || !lambda_T) return bfail(LBM_EINVAL, "NULL buffer");
@@ -581,6 +598,8 @@ int lbm_batch_adjoint_seed(lbm_batch_t *b, const void *f_T, const float *u_targe
 
 int lbm_batch_adjoint_step(lbm_batch_t *b, const void *f_n, const float *lambda_in,
                            float *lambda_out, float *grad_force) {
+  LBM_BREQUIRE_ALIGNED(aligned_to(f_n, kAlignF) && aligned_to(lambda_in, kAlignField) &&
+                       aligned_to(lambda_out, kAlignField) && aligned_to(grad_force, kAlignField));
   int rc = check_b(b);
   if (rc) return rc;
   if (!f_n || !lambda_in || !lambda_out || lambda_in == lambda_out)
@@ -595,6 +614,9 @@ int lbm_batch_adjoint_step(lbm_batch_t *b, const void *f_n, const float *lambda_
 int lbm_batch_adjoint_step_moments(lbm_batch_t *b, const float *rho_n, const float *u_n,
                                    const float *lambda_in, float *lambda_out,
                                    float *grad_force) {
+  LBM_BREQUIRE_ALIGNED(aligned_to(rho_n, kAlignField) && aligned_to(u_n, kAlignField) &&
+                       aligned_to(lambda_in, kAlignField) && aligned_to(lambda_out, kAlignField) &&
+                       aligned_to(grad_force, kAlignField));
   int rc = check_b(b);
   if (rc) return rc;
   if (!rho_n || !u_n || !lambda_in || !lambda_out || lambda_in == lambda_out)
@@ -680,6 +702,8 @@ int lbm_batch_adjoint_run(lbm_batch_t *b, int n, const float *const *rho, const 
 
 int lbm_batch_adjoint_u0(lbm_batch_t *b, const float *lambda0, const float *u0,
                          float *grad_u0) {
+  LBM_BREQUIRE_ALIGNED(aligned_to(lambda0, kAlignField) && aligned_to(u0, kAlignField) &&
+                       aligned_to(grad_u0, kAlignField));
   int rc = check_b(b);
   if (rc) return rc;
   if (!lambda0 || !grad_u0) return bfail(LBM_EINVAL, "NULL buffer");

@@ -125,6 +125,16 @@ int check_bound(const lbm_t *h) {
 
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
+// Alignment the kernels' accesses need (lbm.h conventions); NULL passes here
+// (each call judges NULL itself). Checked before the handle's state, so a
+// misaligned buffer is reported as such whatever the handle.
+constexpr size_t kAlignF = 256, kAlignField = 4, kAlignF64 = 8;
+
+#define LBM_REQUIRE_ALIGNED(cond) \
+  do {                            \
+    if (!(cond)) return fail(LBM_EINVAL, "misaligned device buffer"); \
+  } while (0)
+
 int ensure_scratch(lbm_t *h) {
   int dev = 0;
   LBM_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
@@ -551,6 +561,7 @@ int lbm_current(const lbm_t *h, void **f_cur, void **f_other) {
 }
 
 int lbm_init_equilibrium(lbm_t *h, const float *rho, const float *u) {
+  LBM_REQUIRE_ALIGNED(aligned(rho, kAlignField) && aligned(u, kAlignField));
   int rc = check_bound(h);
   if (rc) return rc;
   StepArgs a = make_args(h, nullptr, h->f[h->cur]);
@@ -567,6 +578,7 @@ int lbm_step(lbm_t *h, int n) {
 }
 
 int lbm_step_moments(lbm_t *h, int n, float *rho, float *u) {
+  LBM_REQUIRE_ALIGNED(aligned(rho, kAlignField) && aligned(u, kAlignField));
   int rc = check_bound(h);
   if (rc) return rc;
   if (n < 1 || !rho || !u) return fail(LBM_EINVAL, "need n >= 1 and rho, u");
@@ -574,11 +586,10 @@ int lbm_step_moments(lbm_t *h, int n, float *rho, float *u) {
 }
 
 int lbm_step_to(lbm_t *h, const void *f_in, void *f_out) {
+  LBM_REQUIRE_ALIGNED(aligned(f_in, kAlignF) && aligned(f_out, kAlignF));
   int rc = check_bound(h);
   if (rc) return rc;
   if (!f_in || !f_out || f_in == f_out) return fail(LBM_EINVAL, "bad buffers");
-  if (!aligned(f_in, 256) || !aligned(f_out, 256))
-    return fail(LBM_EINVAL, "f buffers must be 256-byte aligned");
   StepArgs a = make_args(h, f_in, f_out);
   cudaError_t e = launch_one_step(h, false, a);
   if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
@@ -586,12 +597,11 @@ int lbm_step_to(lbm_t *h, const void *f_in, void *f_out) {
 }
 
 int lbm_step_to_moments(lbm_t *h, const void *f_in, void *f_out, float *rho, float *u) {
+  LBM_REQUIRE_ALIGNED(aligned(f_in, kAlignF) && aligned(f_out, kAlignF) &&
+                      aligned(rho, kAlignField) && aligned(u, kAlignField));
   int rc = check_bound(h);
   if (rc) return rc;
   if (!f_in || !f_out || f_in == f_out || !rho || !u) return fail(LBM_EINVAL, "bad buffers");
-  if (!aligned(f_in, 256) || !aligned(f_out, 256))
-    return fail(LBM_EINVAL, "f buffers must be 256-byte aligned");
-  if (!aligned(rho, 4) || !aligned(u, 4)) return fail(LBM_EINVAL, "rho/u misaligned");
   StepArgs a = make_args(h, f_in, f_out);
   a.rho = rho;
   a.u = u;
@@ -601,11 +611,10 @@ int lbm_step_to_moments(lbm_t *h, const void *f_in, void *f_out, float *rho, flo
 }
 
 int lbm_step_push(lbm_t *h, const void *g_in, void *g_out) {
+  LBM_REQUIRE_ALIGNED(aligned(g_in, kAlignF) && aligned(g_out, kAlignF));
   int rc = check_bound(h);
   if (rc) return rc;
   if (!g_in || !g_out || g_in == g_out) return fail(LBM_EINVAL, "bad buffers");
-  if (!aligned(g_in, 256) || !aligned(g_out, 256))
-    return fail(LBM_EINVAL, "buffers must be 256-byte aligned");
   if (onsite(h)) return fail(LBM_EINVAL, "the push iteration supports halfway walls only");
   StepArgs a = make_args(h, g_in, g_out);
   cudaError_t e = lbm::launch_step_push(h->storage, a, h->bx, h->by, h->stream);
@@ -614,12 +623,11 @@ int lbm_step_push(lbm_t *h, const void *g_in, void *g_out) {
 }
 
 int lbm_stream(lbm_t *h, const void *f_in, void *f_out, int form) {
+  LBM_REQUIRE_ALIGNED(aligned(f_in, kAlignF) && aligned(f_out, kAlignF));
   int rc = check_bound(h);
   if (rc) return rc;
   if (!f_in || !f_out || f_in == f_out) return fail(LBM_EINVAL, "bad buffers");
   if (form < LBM_STREAM_PULL || form > LBM_STREAM_COPY) return fail(LBM_EINVAL, "bad form");
-  if (!aligned(f_in, 256) || !aligned(f_out, 256))
-    return fail(LBM_EINVAL, "buffers must be 256-byte aligned");
   if (onsite(h)) return fail(LBM_EINVAL, "streaming alone supports halfway walls only");
   StepArgs a = make_args(h, f_in, f_out);
   cudaError_t e = lbm::launch_stream(h->storage, a, form, h->bx, h->by, h->stream);
@@ -628,6 +636,7 @@ int lbm_stream(lbm_t *h, const void *f_in, void *f_out, int form) {
 }
 
 int lbm_moments(lbm_t *h, float *rho, float *u, double *mass) {
+  LBM_REQUIRE_ALIGNED(aligned(rho, kAlignField) && aligned(u, kAlignField));
   int rc = check_bound(h);
   if (rc) return rc;
   StepArgs a = make_args(h, nullptr, nullptr);
@@ -841,6 +850,9 @@ int lbm_run_host(lbm_t *h, const float *u0_host, int n, float *rho_host,
 
 int lbm_adjoint_seed(lbm_t *h, const void *f_T, const float *u_target,
                      float *lambda_T, float *grad_force, double *loss) {
+  LBM_REQUIRE_ALIGNED(aligned(f_T, kAlignF) && aligned(u_target, kAlignField) &&
+                      aligned(lambda_T, kAlignField) && aligned(grad_force, kAlignField) &&
+                      aligned(loss, kAlignF64));
   int rc = check_bound(h);
   if (rc) return rc;
   if (h->storage != lbm::kF32) return fail(LBM_EINVAL, "adjoint needs FP32 storage");
@@ -858,6 +870,8 @@ int lbm_adjoint_seed(lbm_t *h, const void *f_T, const float *u_target,
 
 int lbm_adjoint_step(lbm_t *h, const void *f_n, const float *lambda_in,
                      float *lambda_out, float *grad_force) {
+  LBM_REQUIRE_ALIGNED(aligned(f_n, kAlignF) && aligned(lambda_in, kAlignField) &&
+                      aligned(lambda_out, kAlignField) && aligned(grad_force, kAlignField));
   int rc = check_bound(h);
   if (rc) return rc;
   if (h->storage != lbm::kF32) return fail(LBM_EINVAL, "adjoint needs FP32 storage");
@@ -880,6 +894,9 @@ int lbm_adjoint_step(lbm_t *h, const void *f_n, const float *lambda_in,
 
 int lbm_adjoint_step_moments(lbm_t *h, const float *rho_n, const float *u_n,
                              const float *lambda_in, float *lambda_out, float *grad_force) {
+  LBM_REQUIRE_ALIGNED(aligned(rho_n, kAlignField) && aligned(u_n, kAlignField) &&
+                      aligned(lambda_in, kAlignField) && aligned(lambda_out, kAlignField) &&
+                      aligned(grad_force, kAlignField));
   int rc = check_bound(h);
   if (rc) return rc;
   if (h->storage != lbm::kF32) return fail(LBM_EINVAL, "adjoint needs FP32 storage");
@@ -898,6 +915,8 @@ int lbm_adjoint_step_moments(lbm_t *h, const float *rho_n, const float *u_n,
 
 int lbm_adjoint_u0(lbm_t *h, const float *lambda0, const float *u0,
                    float *grad_u0) {
+  LBM_REQUIRE_ALIGNED(aligned(lambda0, kAlignField) && aligned(u0, kAlignField) &&
+                      aligned(grad_u0, kAlignField));
   int rc = check_bound(h);
   if (rc) return rc;
   if (h->storage != lbm::kF32) return fail(LBM_EINVAL, "adjoint needs FP32 storage");

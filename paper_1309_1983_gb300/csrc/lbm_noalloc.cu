@@ -100,10 +100,15 @@ int scratch_address(int dev, double **out) {
 
 }  // namespace
 
+static bool aligned_ptr(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
 extern "C" int lbm_moments_noalloc(const void *f, int nx, int ny, int nz, uint32_t flags,
                                    const float *force, float *rho, float *u, double *mass,
                                    void *stream) {
   if (!f) return lbm::set_error(LBM_EINVAL, "f is NULL");
+  if (!aligned_ptr(f, 256) || !aligned_ptr(force, 4) || !aligned_ptr(rho, 4) ||
+      !aligned_ptr(u, 4) || !aligned_ptr(mass, 8))
+    return lbm::set_error(LBM_EINVAL, "misaligned device buffer");
 #ifdef LBM_CHECK
   if (!lbm::check_record()) return lbm::set_error(LBM_ENOMEM, "check record allocation failed");
 #endif

@@ -252,3 +252,47 @@ def test_check_build_compiles_and_exports_every_symbol():
     missing = [n for n in capi.header_symbols() if not hasattr(chk, n)]
     assert not missing, missing
 
+
+def test_misaligned_device_buffers_are_rejected_before_anything_else(lib):
+    # a misaligned pointer is refused before the handle's state is looked at
+    # (so an unbound handle, or a NULL batch handle, still reports it) and
+    # before any CUDA call: f buffers need 256 bytes, fields and lambda 4,
+    # a device FP64 result 8
+    v = ctypes.c_void_p
+    bad_f, bad_field, ok = v(0x10000 + 16), v(0x10000 + 2), v(0x10000)
+
+    def refused(rc):
+        return rc == capi.LBM_EINVAL and "misaligned" in capi.last_error()
+
+    h = capi.create(8, 8, 8, 0.8, capi.LBM_CAVITY)
+    try:
+        assert refused(lib.lbm_init_equilibrium(h, bad_field, None))
+        assert refused(lib.lbm_step_moments(h, 1, ok, bad_field))
+        assert refused(lib.lbm_step_to(h, bad_f, ok))
+        assert refused(lib.lbm_step_to_moments(h, ok, ok, bad_field, ok))
+        assert refused(lib.lbm_step_push(h, ok, bad_f))
+        assert refused(lib.lbm_stream(h, bad_f, ok, 0))
+        assert refused(lib.lbm_moments(h, bad_field, None, None))
+        assert refused(lib.lbm_adjoint_seed(h, ok, ok, ok, None, v(0x10000 + 4)))
+        assert refused(lib.lbm_adjoint_step(h, ok, bad_field, ok, None))
+        assert refused(lib.lbm_adjoint_step_moments(h, ok, ok, ok, ok, bad_field))
+        assert refused(lib.lbm_adjoint_u0(h, ok, bad_field, ok))
+        # aligned (or NULL) buffers get past the check to the handle's state
+        assert lib.lbm_step_to(h, ok, v(0x20000)) == capi.LBM_EUNBOUND
+        assert lib.lbm_moments(h, None, None, None) == capi.LBM_EUNBOUND
+    finally:
+        lib.lbm_destroy(h)
+    nb = None
+    assert refused(lib.lbm_batch_init_equilibrium(nb, bad_field))
+    assert refused(lib.lbm_batch_step_to(nb, ok, bad_f))
+    assert refused(lib.lbm_batch_step_to_moments(nb, ok, ok, ok, bad_field))
+    assert refused(lib.lbm_batch_adjoint_seed(nb, bad_f, ok, ok, None, None))
+    assert refused(lib.lbm_batch_adjoint_step(nb, ok, ok, bad_field, None))
+    assert refused(lib.lbm_batch_adjoint_step_moments(nb, bad_field, ok, ok, ok, None))
+    assert refused(lib.lbm_batch_adjoint_u0(nb, ok, ok, bad_field))
+    assert refused(lib.lbm_batch_moments(nb, None, bad_field))
+    assert lib.lbm_batch_moments(nb, None, None) == capi.LBM_EINVAL  # the NULL handle
+    assert refused(lib.lbm_moments_noalloc(bad_f, 8, 8, 8, 0, None, None, None, None, None))
+    assert refused(lib.lbm_moments_noalloc(ok, 8, 8, 8, 0, None, None, None,
+                                           v(0x10000 + 4), None))
+
