@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) k_batch_fwd_seq(const BatchArgs a,
       if (k < D.cells) {
         int x, y, z;
         decode(D, k, x, y, z);
-        step_node<0, WALLS, false, MOM, true>(
+        step_node<0, WALLS, false, MOM, true, true>(
             fin + D.foff, fout + D.foff, D.nx, D.ny, D.nz, D.pitch, D.plane, D.walls, D.lidc,
             D.omega, D.kf, nullptr, MOM ? rho + D.coff : nullptr,
             MOM ? u + 3 * (size_t)D.coff : nullptr, D.cells, x, y, z);

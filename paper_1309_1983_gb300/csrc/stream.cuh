@@ -104,6 +104,25 @@ __device__ __forceinline__ void gather_walled(const typename Store<S>::T *__rest
   });
 }
 
+// Pull gather for a node whose warp holds x-wall nodes but no y or z wall
+// node: only the ten e_x != 0 pulls can bounce, e_x = +1 ones on the x = 0
+// node and e_x = -1 ones on the x = nx - 1 node (no lid term: the lid is the
+// z = nz plane).
+template <int S, bool L2ONLY = false>
+__device__ __forceinline__ void gather_xwall(const typename Store<S>::T *__restrict__ fin,
+                                             uint32_t plane, const NodeIdx &n, float (&d)[Q]) {
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (kEx[i] == 0) {
+      d[i] = load_f<S, L2ONLY>(fin + (size_t)i * plane + source_of<i>(n));
+    } else {
+      const bool b = kEx[i] == 1 ? n.x0 : n.x1;
+      const size_t idx = b ? (size_t)kOpp_v<i> * plane + n.c : (size_t)i * plane + source_of<i>(n);
+      d[i] = load_f<S, L2ONLY>(fin + idx);
+    }
+  });
+}
+
 // Value of a bounced pull: f_ibar(x), plus the moving-wall term when the
 // outside source x - e_i lies on the plane z = nz (e_z = -1 at the top face).
 template <int S, bool L2ONLY, int i>
@@ -149,7 +168,13 @@ __device__ __forceinline__ void bounce_fixup(const typename Store<S>::T *__restr
 // moments, equilibrium, BGK (+ Guo force) collide, aligned store of the 19
 // post-collision values at the node; optionally also rho and u into dense
 // fields at index dc. Used by the single-lattice and the batched kernels.
-template <int S, bool WALLS, bool FORCE, bool MOM, bool L2ONLY>
+// With wall_select, VOTE = true chooses the gather per warp (every face where
+// a y or z wall node is present, the x faces only where only x wall nodes
+// are, none elsewhere) instead of selecting on every face in every warp:
+// 4.0% faster for the batched step sequence with moments (the adjoint's
+// segment recompute) and 1.0% without, 0.5% slower for the persistent
+// stepping kernel, which keeps per-node selection.
+template <int S, bool WALLS, bool FORCE, bool MOM, bool L2ONLY, bool VOTE = false>
 __device__ __forceinline__ void step_node(
     const typename Store<S>::T *__restrict__ fin, typename Store<S>::T *__restrict__ fout,
     int nx, int ny, int nz, int pitch, uint32_t plane, uint32_t walls,
@@ -159,7 +184,15 @@ __device__ __forceinline__ void step_node(
   const NodeIdx n = node_index(nx, ny, nz, pitch, walls, x, y, z);
   float d[Q];
   if constexpr (WALLS) {
-    if (wall_select) {
+    if (wall_select && VOTE) {
+      const unsigned m = __activemask();
+      if (__any_sync(m, n.y0 | n.y1 | n.z0 | n.z1))
+        gather_walled<S, L2ONLY>(fin, plane, n, lidc, d);
+      else if (__any_sync(m, n.x0 | n.x1))
+        gather_xwall<S, L2ONLY>(fin, plane, n, d);
+      else
+        gather<S, L2ONLY>(fin, plane, n, d);
+    } else if (wall_select) {
       gather_walled<S, L2ONLY>(fin, plane, n, lidc, d);
     } else {
       gather<S, L2ONLY>(fin, plane, n, d);
