@@ -201,6 +201,17 @@ int lbm_set_block(lbm_t *h, int bx, int by);
  * With nx not a multiple of 4 the padding elements after a row's last node
  * up to the next multiple of 4 are loaded and stored (never used). */
 #define LBM_KERNEL_X4 5
+/* LBM_KERNEL_TMA (16-bit storage, periodic axes and halfway walls; a
+ * measured alternative, slower than LBM_KERNEL_X2 on GB300): the pulled
+ * values of a tile are staged in shared memory by tensor copies (TMA), one
+ * copy per direction, in a persistent producer / consumer pipeline; each
+ * thread then completes two x-adjacent nodes like LBM_KERNEL_X2 (the same
+ * values). The tile is 64 x-consecutive nodes by 4 rows, or by the `by` of
+ * lbm_set_pair_block: 2 selects 128 nodes by 2 rows, 8 selects 64 by 8.
+ * A copy that never lands ends the step with LBM_ETIMEOUT at the next
+ * lbm_sync (bounded waits, never a hang). A step fails with LBM_ECUDA if
+ * the driver offers no tensor-map encoder. */
+#define LBM_KERNEL_TMA 6
 int lbm_set_kernel(lbm_t *h, int variant);
 
 /* How the one-node kernel applies bounce-back: LBM_WALLS_SELECT picks each

@@ -52,6 +52,7 @@ LBM_KERNEL_BULK = 2
 LBM_KERNEL_BULK1 = 3
 LBM_KERNEL_X2 = 4
 LBM_KERNEL_X4 = 5
+LBM_KERNEL_TMA = 6
 
 
 class LBMError(RuntimeError):

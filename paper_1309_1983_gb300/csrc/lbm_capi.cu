@@ -14,6 +14,7 @@
 
 #include "d3q19.cuh"
 #include "internal.h"
+#include "step_tma.h"
 
 using lbm::StepArgs;
 
@@ -167,6 +168,8 @@ cudaError_t launch_one_step(const lbm_t *h, bool mom, const StepArgs &a, cudaStr
     return lbm::launch_step_x2(h->storage, mom, a, h->pbx, h->pby, s);
   if (h->kernel == LBM_KERNEL_X4)
     return lbm::launch_step_x4(h->storage, mom, a, h->pbx, h->pby, s);
+  if (h->kernel == LBM_KERNEL_TMA)
+    return lbm::launch_step_tma(h->storage, mom, a, h->scr.err, h->pby, h->sms, s);
   if ((h->kernel == LBM_KERNEL_BULK || h->kernel == LBM_KERNEL_BULK1) && !mom)
     return lbm::launch_step_bulk(h->storage, a, h->scr.err,
                                  h->kernel == LBM_KERNEL_BULK1 ? 1 : 0, h->sms, s);
@@ -512,12 +515,15 @@ int lbm_set_block(lbm_t *h, int bx, int by) {
 int lbm_set_kernel(lbm_t *h, int variant) {
   if (!h) return fail(LBM_EINVAL, "NULL handle");
   if (variant != LBM_KERNEL_NODE && variant != LBM_KERNEL_PAIR && variant != LBM_KERNEL_BULK &&
-      variant != LBM_KERNEL_BULK1 && variant != LBM_KERNEL_X2 && variant != LBM_KERNEL_X4)
+      variant != LBM_KERNEL_BULK1 && variant != LBM_KERNEL_X2 && variant != LBM_KERNEL_X4 &&
+      variant != LBM_KERNEL_TMA)
     return fail(LBM_EINVAL, "unknown kernel variant");
   if (variant == LBM_KERNEL_PAIR && h->storage == lbm::kF32)
     return fail(LBM_EINVAL, "the shuffle pair kernel needs 16-bit storage");
   if (variant == LBM_KERNEL_X4 && h->storage == lbm::kF32)
     return fail(LBM_EINVAL, "the four-node kernel needs 16-bit storage");
+  if (variant == LBM_KERNEL_TMA && h->storage == lbm::kF32)
+    return fail(LBM_EINVAL, "the tensor-copy staged kernel needs 16-bit storage");
   if (onsite(h) && variant != LBM_KERNEL_X2 && variant != LBM_KERNEL_NODE)
     return fail(LBM_EINVAL, "on-site walls run on LBM_KERNEL_X2 or LBM_KERNEL_NODE");
   h->kernel = variant;

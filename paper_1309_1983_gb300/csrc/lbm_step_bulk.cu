@@ -24,6 +24,7 @@
 #include "d3q19.cuh"
 #include "internal.h"
 #include "stream.cuh"
+#include "tma.cuh"
 
 namespace lbm {
 
@@ -32,63 +33,6 @@ namespace bulk {
 constexpr int TX = 128;
 constexpr int kConsumers = TX;
 constexpr int kThreads = TX + 32;  // + one producer warp
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s per wait
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait for the phase with the given parity, for at most kWaitLimitNs of wall
-// clock time (try_wait itself suspends briefly between polls); false on
-// timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = now_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (now_ns() - t0 > kWaitLimitNs) return false;
-  return true;
-}
-
-__device__ __forceinline__ void bulk_copy(void *dst_smem, const void *src, uint32_t bytes,
-                                          uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(smem_addr(dst_smem)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
 
 struct TileCoord {
   int x0, y0, z;
@@ -132,10 +76,10 @@ __global__ void __launch_bounds__(bulk::kThreads) k_step_bulk(const BulkArgs A) 
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      bulk::mbar_init(&full[s], 1);
-      bulk::mbar_init(&empty[s], bulk::kConsumers);
+      tma::mbar_init(&full[s], 1);
+      tma::mbar_init(&empty[s], bulk::kConsumers);
     }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tma::fence_barrier_init();
   }
   __syncthreads();
 
@@ -146,7 +90,7 @@ __global__ void __launch_bounds__(bulk::kThreads) k_step_bulk(const BulkArgs A) 
     bool ok = true;
     for (int t = blockIdx.x; t < A.ntiles && ok; t += gridDim.x, ++k) {
       const int s = k % STAGES;
-      if (k >= STAGES && !bulk::mbar_wait(&empty[s], ((k / STAGES) - 1) & 1)) {
+      if (k >= STAGES && !tma::mbar_wait(&empty[s], ((k / STAGES) - 1) & 1)) {
         LBM_ATOMIC_OR(A.err, (int)kErrTimeout);
         ok = false;
         break;
@@ -156,7 +100,7 @@ __global__ void __launch_bounds__(bulk::kThreads) k_step_bulk(const BulkArgs A) 
       const int hi = min(tc.x0 + bulk::TX + H, a.pitch);
       const int nrows = min(TY, a.ny - tc.y0);
       const uint32_t bytes = (uint32_t)(Q * nrows * (hi - lo) * EB);
-      bulk::mbar_expect_tx(&full[s], bytes);
+      tma::mbar_expect_tx(&full[s], bytes);
       T *st = rows + (size_t)s * STAGE_ELEMS;
       const int zm = tc.z == 0 ? a.nz - 1 : tc.z - 1, zp = tc.z == a.nz - 1 ? 0 : tc.z + 1;
       for (int r = 0; r < nrows; ++r) {
@@ -172,7 +116,7 @@ __global__ void __launch_bounds__(bulk::kThreads) k_step_bulk(const BulkArgs A) 
           // a refused copy (check build) leaves the stage incomplete: the
           // consumers' bounded wait then reports kErrTimeout
           if (LBM_CHK(src, (uint32_t)((hi - lo) * EB), 16u, kChkRead))
-            bulk::bulk_copy(dst, src, (uint32_t)((hi - lo) * EB), &full[s]);
+            tma::bulk_copy(dst, src, (uint32_t)((hi - lo) * EB), &full[s]);
         });
       }
     }
@@ -180,7 +124,7 @@ __global__ void __launch_bounds__(bulk::kThreads) k_step_bulk(const BulkArgs A) 
     // still writing shared memory when the block exits
     const int last = k;
     for (int j = max(0, last - STAGES); j < last; ++j)
-      bulk::mbar_wait(&full[j % STAGES], (j / STAGES) & 1);
+      tma::mbar_wait(&full[j % STAGES], (j / STAGES) & 1);
     return;
   }
 
@@ -188,7 +132,7 @@ __global__ void __launch_bounds__(bulk::kThreads) k_step_bulk(const BulkArgs A) 
   int k = 0;
   for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++k) {
     const int s = k % STAGES;
-    if (!bulk::mbar_wait(&full[s], (k / STAGES) & 1)) {
+    if (!tma::mbar_wait(&full[s], (k / STAGES) & 1)) {
       LBM_ATOMIC_OR(A.err, (int)kErrTimeout);
       return;
     }
@@ -235,7 +179,7 @@ __global__ void __launch_bounds__(bulk::kThreads) k_step_bulk(const BulkArgs A) 
         Store<S>::st(fout + (size_t)i * a.plane + n.c, d[i]);
       });
     }
-    bulk::mbar_arrive(&empty[s]);
+    tma::mbar_arrive(&empty[s]);
   }
 }
 

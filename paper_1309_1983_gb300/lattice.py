@@ -124,7 +124,8 @@ class Lattice:
         (rows staged in shared memory by bulk copies)."""
         v = {"node": capi.LBM_KERNEL_NODE, "pair": capi.LBM_KERNEL_PAIR,
              "bulk": capi.LBM_KERNEL_BULK, "bulk1": capi.LBM_KERNEL_BULK1,
-             "x2": capi.LBM_KERNEL_X2, "x4": capi.LBM_KERNEL_X4}[variant]
+             "x2": capi.LBM_KERNEL_X2, "x4": capi.LBM_KERNEL_X4,
+             "tma": capi.LBM_KERNEL_TMA}[variant]
         capi.call("lbm_set_kernel", self._h, v)
 
     def set_graph_steps(self, steps):

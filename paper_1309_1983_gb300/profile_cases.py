@@ -21,7 +21,7 @@ import sys
 
 
 def step(geometry: str = "cavity", storage: str = "f16", n: int = 256, launches: int = 4,
-         tau: float = 0.55, kernel: str = "x2", onsite: bool = False) -> None:
+         tau: float = 0.55, kernel: str = "x2", onsite: bool = False, rows: int = 0) -> None:
     import torch
     from .lattice import Lattice
     walls = (geometry == "cavity",) * 3
@@ -29,6 +29,8 @@ def step(geometry: str = "cavity", storage: str = "f16", n: int = 256, launches:
                 storage=storage, onsite=onsite)
     L.set_graph_steps(0)
     L.set_kernel(kernel)
+    if rows:
+        L.set_pair_block(32, rows)
     L.init_equilibrium()
     for _ in range(launches):
         L.step(1)
@@ -73,7 +75,9 @@ def main(argv=None) -> int:
     s.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16"])
     s.add_argument("--n", type=int, default=256)
     s.add_argument("--launches", type=int, default=4)
-    s.add_argument("--kernel", default="x2", choices=["x2", "x4", "node"])
+    s.add_argument("--kernel", default="x2", choices=["x2", "x4", "node", "tma"])
+    s.add_argument("--rows", type=int, default=0,
+                   help="tile rows of the tma kernel (pair-block rows; 0: the default)")
     s.add_argument("--onsite", action="store_true")
     s.add_argument("--tau", type=float, default=0.55)
     b = sub.add_parser("batch-adjoint")
@@ -81,7 +85,8 @@ def main(argv=None) -> int:
     b.add_argument("--launches", type=int, default=2)
     a = p.parse_args(argv)
     if a.case == "step":
-        step(a.geometry, a.storage, a.n, a.launches, tau=a.tau, kernel=a.kernel, onsite=a.onsite)
+        step(a.geometry, a.storage, a.n, a.launches, tau=a.tau, kernel=a.kernel, onsite=a.onsite,
+             rows=a.rows)
     else:
         batch_adjoint(a.steps, a.launches)
     print("ok")

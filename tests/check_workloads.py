@@ -220,7 +220,8 @@ def workloads():
     w = {}
     for storage in ("f32", "f16", "bf16"):
         for geom in ("periodic", "cavity", "channel"):
-            kernels = ["x2", "node", "bulk", "bulk1"] + (["x4", "pair"] if storage != "f32" else [])
+            kernels = ["x2", "node", "bulk", "bulk1"] + (["x4", "pair", "tma"] if storage != "f32"
+                                                         else [])
             for k in kernels:
                 w[f"fwd_{geom}_{storage}_{k}"] = (forward, (geom, storage, k))
         w[f"fwd_cavity_{storage}_x2_force"] = (forward, ("cavity", storage, "x2", True))
@@ -231,6 +232,9 @@ def workloads():
         w[f"onsite_{storage}_x2"] = (forward, ("cavity", storage, "x2", True, True))
         w[f"onsite_{storage}_node"] = (forward, ("cavity", storage, "node", True, True))
         w[f"graph_cavity_{storage}"] = (forward, ("cavity", storage, "x2", False, False, None, 2))
+        if storage != "f32":
+            w[f"graph_cavity_{storage}_tma"] = (forward, ("cavity", storage, "tma", True, False,
+                                                          None, 2))
         w[f"streams_push_{storage}"] = (streams_and_push, (storage,))
         w[f"noalloc_{storage}"] = (noalloc, (storage,))
     w["run_host"] = (run_host, ())

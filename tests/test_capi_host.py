@@ -192,7 +192,7 @@ def test_kernel_variants_need_matching_storage(lib):
         for v in (capi.LBM_KERNEL_PAIR, capi.LBM_KERNEL_X2):
             assert lib.lbm_set_kernel(h16, v) == 0
         assert lib.lbm_set_kernel(h32, capi.LBM_KERNEL_X2) == 0
-        assert lib.lbm_set_kernel(h16, 6) == capi.LBM_EINVAL  # unknown variant
+        assert lib.lbm_set_kernel(h16, 7) == capi.LBM_EINVAL  # unknown variant
         assert lib.lbm_set_kernel(h32, capi.LBM_KERNEL_NODE) == 0
     finally:
         lib.lbm_destroy(h32)
@@ -232,6 +232,25 @@ def test_four_node_kernel_needs_sixteen_bit_storage_and_halfway_walls(lib):
     h = capi.create(16, 8, 8, 0.8, capi.LBM_STORE_F16 | capi.LBM_CAVITY | capi.LBM_WALLS_ONSITE)
     try:
         assert lib.lbm_set_kernel(h, capi.LBM_KERNEL_X4) == capi.LBM_EINVAL
+    finally:
+        lib.lbm_destroy(h)
+
+
+def test_tensor_copy_kernel_needs_sixteen_bit_storage_and_halfway_walls(lib):
+    h = capi.create(16, 8, 8, 0.8, capi.LBM_STORE_F32)
+    try:
+        assert lib.lbm_set_kernel(h, capi.LBM_KERNEL_TMA) == capi.LBM_EINVAL
+    finally:
+        lib.lbm_destroy(h)
+    for st in (capi.LBM_STORE_F16, capi.LBM_STORE_BF16):
+        h = capi.create(16, 8, 8, 0.8, st | capi.LBM_CAVITY)
+        try:
+            assert lib.lbm_set_kernel(h, capi.LBM_KERNEL_TMA) == capi.LBM_OK
+        finally:
+            lib.lbm_destroy(h)
+    h = capi.create(16, 8, 8, 0.8, capi.LBM_STORE_F16 | capi.LBM_CAVITY | capi.LBM_WALLS_ONSITE)
+    try:
+        assert lib.lbm_set_kernel(h, capi.LBM_KERNEL_TMA) == capi.LBM_EINVAL
     finally:
         lib.lbm_destroy(h)
 

@@ -107,12 +107,13 @@ def test_forward_kernels_write_only_node_elements(storage, geom, shape):
     check("init", False)
     L.step(3)  # default two-node kernel
     check("x2", True)
-    kernels = ["node", "bulk", "bulk1"] + (["pair", "x4"] if storage != "f32" else [])
+    kernels = ["node", "bulk", "bulk1"] + (["pair", "tma", "x4"] if storage != "f32" else [])
     for k in kernels:
         L.set_kernel(k)
         if k == "x4":
             group[0] = 4
         L.step(2)
+        L.sync()
         check(k, True)
     L.set_kernel("x2")
     L.set_graph_steps(4)
