@@ -22,7 +22,9 @@
 // the face values written into the stage by the producer warp, face loads
 // issued before the stage wait, a 64-register cap with 6 blocks per SM, 2
 // or 4 stages, L2 promotion of 128 or 256 bytes) were all slower; the
-// two-node kernel stays the default.
+// two-node kernel stays the default. (A two-node kernel taking two pairs
+// per thread in two rows, loads of both issued first, 152 bytes in flight a
+// thread, measured no faster either: 82.1 against 83.3 GLUPS.)
 //
 // Tiles: 64 x-consecutive nodes (32 pairs) of TY rows in one z plane, or
 // 128 nodes of 2 rows. For each direction i one tensor copy brings the
