@@ -206,8 +206,9 @@ int lbm_set_block(lbm_t *h, int bx, int by);
  * values of a tile are staged in shared memory by tensor copies (TMA), one
  * copy per direction, in a persistent producer / consumer pipeline; each
  * thread then completes two x-adjacent nodes like LBM_KERNEL_X2 (the same
- * values). The tile is 64 x-consecutive nodes by 4 rows, or by the `by` of
- * lbm_set_pair_block: 2 selects 128 nodes by 2 rows, 8 selects 64 by 8.
+ * values). The tile is 64 x-consecutive nodes by 4 rows; the `by` of
+ * lbm_set_pair_block selects others: 1 gives 128 nodes by 2 rows, 8 gives
+ * 64 by 8.
  * A copy that never lands ends the step with LBM_ETIMEOUT at the next
  * lbm_sync (bounded waits, never a hang). A step fails with LBM_ECUDA if
  * the driver offers no tensor-map encoder. */

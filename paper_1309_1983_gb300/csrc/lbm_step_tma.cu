@@ -21,7 +21,8 @@
 // variants tried (the tile seams read from global memory instead of halos,
 // the face values written into the stage by the producer warp, face loads
 // issued before the stage wait, a 64-register cap with 6 blocks per SM, 2
-// or 4 stages, L2 promotion of 128 or 256 bytes) were all slower; the
+// or 4 stages, L2 promotion of 128 or 256 bytes, 16-value halos) were all
+// slower or no faster; the
 // two-node kernel stays the default. (A two-node kernel taking two pairs
 // per thread in two rows, loads of both issued first, 152 bytes in flight a
 // thread, measured no faster either: 82.1 against 83.3 GLUPS.)
@@ -448,13 +449,14 @@ cudaError_t tma_dispatch(bool mom, TmaArgs &A, int sms, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
-// Tile shapes (nodes along x, rows) by the `by` of the launch: 2 -> 128 x 2,
-// 8 -> 64 x 8, else 64 x 4; three pipeline stages each.
+// Tile shapes (nodes along x, rows) by the `by` of the launch: 1 -> 128 x 2,
+// 8 -> 64 x 8, else (the default pair block's 2 included) 64 x 4, the
+// fastest measured; three pipeline stages each.
 struct Shape {
   int tx, ty;
 };
 Shape tma_shape(int by) {
-  return by == 2 ? Shape{128, 2} : by == 8 ? Shape{64, 8} : Shape{64, 4};
+  return by == 1 ? Shape{128, 2} : by == 8 ? Shape{64, 8} : Shape{64, 4};
 }
 
 template <int S>

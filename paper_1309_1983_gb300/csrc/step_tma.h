@@ -7,7 +7,7 @@
 namespace lbm {
 
 // 16-bit storage with the pulled values staged in shared memory by tensor
-// copies: persistent over tiles whose shape `by` selects (2: 128 nodes x 2
+// copies: persistent over tiles whose shape `by` selects (1: 128 nodes x 2
 // rows, 8: 64 x 8, any other value 64 x 4), periodic axes and halfway walls
 // (not the on-site rule). err receives kErrTimeout if a bounded mbarrier
 // wait gave up; cudaErrorNotSupported if the driver has no tensor-map
