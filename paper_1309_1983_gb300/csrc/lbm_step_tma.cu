@@ -224,7 +224,8 @@ __device__ __forceinline__ void tma_produce(const TmaArgs &A, uint32_t sbase, ui
   tile::Walk w;
   w.start(blockIdx.x, A.nxt, A.nyt, a.z0);
   int k = 0;
-  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++k, w.next(A.gx, A.gy, A.gz, A.nxt, A.nyt)) {
+  for (int t = blockIdx.x; t < A.ntiles;
+       t += gridDim.x, ++k, w.next(A.gx, A.gy, A.gz, A.nxt, A.nyt)) {
     const int s = k % STAGES;
     if (k >= STAGES && !tma::mbar_wait(&empty[s], ((k / STAGES) - 1) & 1)) {
       LBM_ATOMIC_OR(A.err, (int)kErrTimeout);
@@ -268,7 +269,8 @@ __device__ __forceinline__ void tma_consume(const TmaArgs &A, const unsigned cha
   tile::Walk w;
   w.start(blockIdx.x, A.nxt, A.nyt, a.z0);
   int k = 0;
-  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++k, w.next(A.gx, A.gy, A.gz, A.nxt, A.nyt)) {
+  for (int t = blockIdx.x; t < A.ntiles;
+       t += gridDim.x, ++k, w.next(A.gx, A.gy, A.gz, A.nxt, A.nyt)) {
     const int s = k % STAGES;
     if (!tma::mbar_wait(&full[s], (k / STAGES) & 1)) {
       LBM_ATOMIC_OR(A.err, (int)kErrTimeout);
