@@ -573,12 +573,15 @@ int lbm_batch_set_f(lbm_batch_t *b, int dom, const double *host_f);
  * 2 write, 3 read-modify-write) the first of them (zeros if none). Any
  * pointer may be NULL.
  * lbm_check_reset: waits for the device and zeroes the record.
- * lbm_check_narrow: every table built from now on ends each range `bytes`
- * before the end of the buffer it describes (0: exact extents again), so
- * that the kernels' accesses to the last `bytes` of every buffer are refused
- * (and not made): a way to see refusals detected and reported while every
- * access that is made stays inside its buffer. Launches replayed from CUDA
- * graphs captured earlier keep the tables they were captured with. */
+ * lbm_check_narrow: every table built from now on ends each range longer
+ * than `bytes` that many bytes before the end of the buffer it describes (0:
+ * exact extents again), so that the kernels' accesses to the last `bytes`
+ * of every such buffer are refused (and not made): a way to see refusals
+ * detected and reported while every access that is made stays inside its
+ * buffer. Ranges of at most `bytes` (the error word, small tables) keep
+ * their extent, so that a launch can still report what the refusals caused
+ * (a bounded wait that gave up). Launches replayed from CUDA graphs
+ * captured earlier keep the tables they were captured with. */
 int lbm_check_status(unsigned long long *refused, unsigned long long *first_addr,
                      unsigned int *first_bytes, unsigned int *first_kind);
 int lbm_check_reset(void);

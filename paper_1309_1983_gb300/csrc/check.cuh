@@ -88,7 +88,8 @@ static __device__ __noinline__ bool check_access(const void *p, unsigned bytes, 
 
 // The process's record (allocated on first use; lbm_capi.cu).
 CheckRecord *check_record();
-// Ranges narrowed by this many bytes at their end (lbm_check_narrow).
+// Ranges longer than this many bytes are narrowed by it at their end
+// (lbm_check_narrow).
 size_t check_narrow_bytes();
 
 // Null or empty ranges are left out; a range given twice gets the union of
@@ -101,7 +102,7 @@ static inline cudaError_t check_table(cudaStream_t s, const CheckRange *rs, int 
     const CheckRange &r = rs[k];
     if (r.p == nullptr || r.bytes == 0) continue;
     const unsigned long long lo = reinterpret_cast<unsigned long long>(r.p);
-    const unsigned long long hi = lo + (r.bytes > narrow ? r.bytes - narrow : 0);
+    const unsigned long long hi = lo + (r.bytes > narrow ? r.bytes - narrow : r.bytes);
     int j = 0;
     while (j < t.n && !(t.lo[j] == lo && t.hi[j] == hi)) ++j;
     if (j == t.n) {

@@ -13,7 +13,8 @@ test named by LBM_LIBRARY:
 --narrow B ends every range of every launch table B bytes early
 (lbm_check_narrow) for one plain step of a periodic FP32 lattice, and
 records the first refused access and the tails of the buffers it could lie
-in. --large runs the benchmark's sizes instead (one step of 384^3 periodic
+in; --narrow-tma B does the same for one step of the tensor-copy staged
+kernel (FP16) and records the error code of the lbm_sync after it. --large runs the benchmark's sizes instead (one step of 384^3 periodic
 FP32, 384^3 cavity FP16 with halfway and with on-site walls, the 1024^3
 FP32 cavity (163 GB of f), and the 64-cavity batch: persistent steps, a
 step sequence with moments and a reverse sequence) and records only the
@@ -271,6 +272,39 @@ def narrow(nbytes):
         L.close()
 
 
+def narrow_tma(nbytes):
+    """One step of the tensor-copy staged kernel (periodic FP16) with every
+    table range ended nbytes early: the copies reading a tail are not issued,
+    so their stages never complete and the bounded waits end the launch with
+    a timeout instead of a hang. Returns the refusals, the buffer tails and
+    the error code of the following lbm_sync."""
+    L = lattice("periodic", "f16")
+    try:
+        nx, ny, nz = SHAPE
+        L.set_kernel("tma")
+        L.init_equilibrium(u=rand_field((3, nz, ny, nx), 33, 0.02))
+        refused()
+        capi.call("lbm_check_narrow", nbytes)
+        try:
+            L.step(1)
+            torch.cuda.synchronize()
+            n, addr, size, kind = capi.check_status()
+        finally:
+            capi.call("lbm_check_narrow", 0)
+        code = 0
+        try:
+            L.sync()
+        except capi.LBMError as e:
+            code = e.code
+        capi.call("lbm_check_reset")
+        fb = L.layout.f_bytes
+        tails = [[t.data_ptr() + fb - nbytes, t.data_ptr() + fb] for t in (L.f_a, L.f_b)]
+        return {"refused": n, "first": addr, "bytes": size, "kind": kind, "tails": tails,
+                "sync": code}
+    finally:
+        L.close()
+
+
 def large():
     from paper_1309_1983_gb300 import workloads as W
     res = {}
@@ -322,6 +356,8 @@ def main(argv):
     res = {"library": os.path.basename(capi.LIB_PATH), "checked": CHECKED}
     if "--narrow" in argv:
         res["narrow"] = narrow(int(argv[argv.index("--narrow") + 1]))
+    elif "--narrow-tma" in argv:
+        res["narrow_tma"] = narrow_tma(int(argv[argv.index("--narrow-tma") + 1]))
     elif "--large" in argv:
         if CHECKED:
             refused()

@@ -21,7 +21,10 @@ process of its own. The tests check that
   step's accesses to those tails are refused and the first one is reported
   with its address inside one of the two f buffers' tails: refusals are
   detected, and the refused accesses are not made, so every access that is
-  made stays inside its real buffer.
+  made stays inside its real buffer;
+* the same narrowing makes the tensor-copy staged kernel skip the copies
+  that read a tail, and its bounded waits end the step with LBM_ETIMEOUT
+  (reported by lbm_sync) instead of hanging.
 """
 
 import json
@@ -88,6 +91,18 @@ def test_narrowed_tables_are_refused_and_reported(libs, tmp_path):
     assert res["refused"] > 0, res
     assert any(lo <= res["first"] < hi for lo, hi in res["tails"]), res
     assert res["bytes"] in (4, 8) and res["kind"] in (1, 2), res
+
+
+def test_refused_tensor_copy_ends_in_a_timeout_not_a_hang(libs, tmp_path):
+    """A tensor copy that the check build refuses is never issued, so its
+    pipeline stage never completes: the bounded mbarrier waits end the launch
+    and the next lbm_sync reports LBM_ETIMEOUT."""
+    from paper_1309_1983_gb300 import capi
+    res = _run(tmp_path / "narrow_tma.json", libs[1], "--narrow-tma", "64")["narrow_tma"]
+    assert res["refused"] > 0, res
+    assert any(lo <= res["first"] < hi for lo, hi in res["tails"]), res
+    assert res["bytes"] in (2, 4) and res["kind"] in (1, 2), res
+    assert res["sync"] == capi.LBM_ETIMEOUT, res
 
 
 def test_checked_build_refuses_no_access_at_full_size(libs, tmp_path):
