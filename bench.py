@@ -380,8 +380,9 @@ def capacity_workload(torch, n=1024, steps=20):
 
 def streaming_ablation(torch, n, steps=50):
     """Sec. 4.3 redone on this GPU: streaming alone as an unshifted copy, a
-    gather (misaligned reads) and a scatter (misaligned writes), and the full
-    step in pull order (Alg. 3) and push order (Alg. 2); FP32, periodic."""
+    gather (misaligned reads; also with L2-only loads, no read-only cache)
+    and a scatter (misaligned writes), and the full step in pull order
+    (Alg. 3) and push order (Alg. 2); FP32, periodic."""
     from paper_1309_1983_gb300.lattice import Lattice
     L = Lattice(n, n, n, TAU)
     L.init_equilibrium()
@@ -390,6 +391,7 @@ def streaming_ablation(torch, n, steps=50):
     out = {}
     cases = (("copy", lambda x, y: L.streaming(x, y, "copy")),
              ("stream_gather", lambda x, y: L.streaming(x, y, "pull")),
+             ("stream_gather_l2_only", lambda x, y: L.streaming(x, y, "pull_l2")),
              ("stream_scatter", lambda x, y: L.streaming(x, y, "push")),
              ("step_pull", lambda x, y: L.step_to(x, y)),
              ("step_push", lambda x, y: L.step_push(x, y)))

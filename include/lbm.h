@@ -300,10 +300,14 @@ int lbm_step_push(lbm_t *h, const void *g_in, void *g_out);
  * LBM_STREAM_PULL gathers (misaligned reads, aligned writes),
  * LBM_STREAM_PUSH scatters (aligned reads, misaligned writes); both give the
  * same result. LBM_STREAM_COPY copies the 19 planes unshifted (the
- * bandwidth reference of the aligned/misaligned comparison, Sec. 4.3). */
+ * bandwidth reference of the aligned/misaligned comparison, Sec. 4.3).
+ * LBM_STREAM_PULL_L2 gathers like LBM_STREAM_PULL with loads that bypass
+ * the L1 and read-only caches (ld.global.cg): the paper's misaligned reads
+ * without the read-only data cache (Sec. 4.3). */
 #define LBM_STREAM_PULL 0
 #define LBM_STREAM_PUSH 1
 #define LBM_STREAM_COPY 2
+#define LBM_STREAM_PULL_L2 3
 int lbm_stream(lbm_t *h, const void *f_in, void *f_out, int form);
 
 /* Moments of the current (post-collision) state: rho = sum f_i (Eq. 6),

@@ -46,6 +46,7 @@ LBM_WALLS_SELECT = 2
 LBM_STREAM_PULL = 0
 LBM_STREAM_PUSH = 1
 LBM_STREAM_COPY = 2
+LBM_STREAM_PULL_L2 = 3
 LBM_KERNEL_NODE = 0
 LBM_KERNEL_PAIR = 1
 LBM_KERNEL_BULK = 2

@@ -633,7 +633,7 @@ int lbm_stream(lbm_t *h, const void *f_in, void *f_out, int form) {
   int rc = check_bound(h);
   if (rc) return rc;
   if (!f_in || !f_out || f_in == f_out) return fail(LBM_EINVAL, "bad buffers");
-  if (form < LBM_STREAM_PULL || form > LBM_STREAM_COPY) return fail(LBM_EINVAL, "bad form");
+  if (form < LBM_STREAM_PULL || form > LBM_STREAM_PULL_L2) return fail(LBM_EINVAL, "bad form");
   if (onsite(h)) return fail(LBM_EINVAL, "streaming alone supports halfway walls only");
   StepArgs a = make_args(h, f_in, f_out);
   cudaError_t e = lbm::launch_stream(h->storage, a, form, h->bx, h->by, h->stream);

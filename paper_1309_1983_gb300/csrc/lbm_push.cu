@@ -12,7 +12,9 @@
 //
 // k_stream applies P alone: form 0 gathers (misaligned reads, aligned
 // writes), form 1 scatters (aligned reads, misaligned writes); form 2 is an
-// unshifted copy of the 19 planes, the bandwidth reference.
+// unshifted copy of the 19 planes, the bandwidth reference; form 3 gathers
+// with L2-only loads (no L1 or read-only cache: the paper's measurement of
+// misaligned reads without the read-only data cache).
 #include "d3q19.cuh"
 #include "internal.h"
 #include "stream.cuh"
@@ -80,12 +82,18 @@ __global__ void __launch_bounds__(256) k_stream(const StepArgs a, int form) {
   const T *__restrict__ fin = static_cast<const T *>(a.fin);
   T *__restrict__ fout = static_cast<T *>(a.fout);
   const NodeIdx n = node_index(a.nx, a.ny, a.nz, a.pitch, a.walls, x, y, z);
-  if (form == 0) {  // gather: misaligned reads, aligned writes
+  if (form == 0 || form == 3) {  // gather: misaligned reads, aligned writes
     float d[Q];
-    if (a.walls)
+    if (form == 3) {  // through L2 only
+      if (a.walls)
+        gather_walled<S, true>(fin, a.plane, n, a.lidc, d);
+      else
+        gather<S, true>(fin, a.plane, n, d);
+    } else if (a.walls) {
       gather_walled<S>(fin, a.plane, n, a.lidc, d);
-    else
+    } else {
       gather<S>(fin, a.plane, n, d);
+    }
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
       Store<S>::st(fout + (size_t)i * a.plane + n.c, d[i]);

@@ -190,9 +190,10 @@ class Lattice:
         capi.call("lbm_step_push", self._h, _ptr(g_in), _ptr(g_out))
 
     def streaming(self, f_in, f_out, form="pull"):
-        """f_out = P f_in; form "pull", "push" or "copy" (unshifted)."""
+        """f_out = P f_in; form "pull", "push", "pull_l2" (the gather through
+        L2 only) or "copy" (unshifted)."""
         v = {"pull": capi.LBM_STREAM_PULL, "push": capi.LBM_STREAM_PUSH,
-             "copy": capi.LBM_STREAM_COPY}[form]
+             "copy": capi.LBM_STREAM_COPY, "pull_l2": capi.LBM_STREAM_PULL_L2}[form]
         capi.call("lbm_stream", self._h, _ptr(f_in), _ptr(f_out), v)
 
     def buffer_to_numpy(self, buf):

@@ -108,7 +108,7 @@ def streams_and_push(storage):
         L.init_equilibrium(u=rand_field((3, nz, ny, nx), 5, 0.02))
         a, b = L.current_buffers()
         out = []
-        for form in ("pull", "push", "copy"):
+        for form in ("pull", "push", "copy", "pull_l2"):
             L.streaming(a, b, form)
             out.append(b.clone())
         L.step_push(a, b)

@@ -136,7 +136,7 @@ def test_forward_kernels_write_only_node_elements(storage, geom, shape):
     assert _guard_intact(rf, 4 * cells) and _guard_intact(uf, 12 * cells), "noalloc"
 
     cur, other = L.current_buffers()
-    for form in ("pull", "push", "copy"):
+    for form in ("pull", "push", "copy", "pull_l2"):
         L.streaming(cur, other, form)
         check("stream " + form, True)
     L.step_push(cur, other)

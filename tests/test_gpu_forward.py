@@ -308,9 +308,9 @@ def test_bulk_kernel_is_bit_identical_to_node_kernel(storage, variant, geom, sha
 @pytest.mark.parametrize("geom", sorted(GEOMS))
 @pytest.mark.parametrize("shape", [(37, 11, 9), (1, 7, 6), (5, 1, 1)], ids=lambda s: "x".join(map(str, s)))
 def test_streaming_forms_equal_oracle_stream(geom, shape):
-    """lbm_stream: the gather (pull) and scatter (push) forms both equal the
-    oracle's stream pass (boundary rule included); the copy form is the
-    identity."""
+    """lbm_stream: the gather (pull, also through L2 only) and scatter (push)
+    forms all equal the oracle's stream pass (boundary rule included); the
+    copy form is the identity."""
     nx, ny, nz = shape
     g = GEOMS[geom]
     L = _lat(nx, ny, nz, 0.7, g["walls"], g["lid"])
@@ -320,7 +320,7 @@ def test_streaming_forms_equal_oracle_stream(geom, shape):
     cur, _ = L.current_buffers()
     ref = O.stream(OL, L.get_f())
     out = torch.empty_like(cur)
-    for form in ("pull", "push"):
+    for form in ("pull", "push", "pull_l2"):
         L.streaming(cur, out, form)
         assert np.abs(L.buffer_to_numpy(out) - ref).max() <= 1e-7, form
     L.streaming(cur, out, "copy")
