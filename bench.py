@@ -47,8 +47,9 @@ def parse():
     p.add_argument("--n", type=int, default=N_DEFAULT, help="lattice edge (cube)")
     p.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     p.add_argument("--extras", default="all",
-                   help="comma list of secondary workloads: storage,streaming,adjoint,batched,sweep "
-                        "(or all, the default, for these five) and capacity (1024^3, opt-in)")
+                   help="comma list of secondary workloads: storage,streaming,adjoint,batched,sweep,"
+                        "tables (the paper's block-size x lattice-size experiment) (or all, the "
+                        "default, for these six) and capacity (1024^3, opt-in)")
     p.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                    help="storage of the main timed workload (profiling runs)")
     p.add_argument("--geometry", default="periodic", choices=["periodic", "cavity"],
@@ -300,6 +301,41 @@ def extra_workloads(torch, n, steps=100, warmup=10):
         out[name] = {"mlups": round(mlups, 1), "bytes_per_lu": PM.bytes_per_update(eb),
                      "gbs": round(PM.achieved_gbs(mlups, PM.bytes_per_update(eb)), 1),
                      "steps": steps}
+        L.close()
+        del L
+        torch.cuda.empty_cache()
+    return out
+
+
+def paper_tables(torch, sizes=(64, 96, 128, 160, 192, 224, 256), steps=100):
+    """The paper's throughput experiment (Sec. 6, Tables 1 and 2) on this
+    GPU: the lid-driven cavity in FP32 (tau = 0.6, lid 0.05), 100 single
+    launches per configuration, for cubic lattices of 64^3 to 256^3 and
+    blocks of 32, 64, 128 and 256 threads along x with the one-node kernel
+    (the paper's one node per thread), and the default two-node kernel;
+    per-launch MLUPS as mean, standard deviation and best (the tables' style).
+    The lattices up to 192^3 (0.8 GB per f copy and less) are partly
+    resident in the 129 MB L2 only below 96^3."""
+    import statistics
+    from paper_1309_1983_gb300.lattice import Lattice
+    out = {}
+    for n in sizes:
+        L = Lattice(n, n, n, 0.6, walls=(True, True, True), lid=(0.05, 0.0, 0.0))
+        L.set_graph_steps(0)
+        row = {}
+        for name, kern, bx in (("node_32", "node", 32), ("node_64", "node", 64),
+                               ("node_128", "node", 128), ("node_256", "node", 256),
+                               ("x2", "x2", 0)):
+            L.set_kernel(kern)
+            if bx:
+                L.set_block(bx, 1)
+            L.init_equilibrium()
+            L.step(5)
+            _, per = timed_steps(L, steps, torch)
+            m = [n ** 3 / (t / 1e3) / 1e6 for t in per]
+            row[name] = {"mean": round(statistics.mean(m), 1), "sd": round(statistics.pstdev(m), 1),
+                         "best": round(max(m), 1)}
+        out[str(n)] = row
         L.close()
         del L
         torch.cuda.empty_cache()
@@ -647,12 +683,14 @@ def run_ours(args):
         del L, u0
         torch.cuda.empty_cache()
         want = set(args.extras.split(",")) if args.extras != "all" else {
-            "storage", "streaming", "adjoint", "batched", "sweep"}
+            "storage", "streaming", "adjoint", "batched", "sweep", "tables"}
         extras = {}
         if "sweep" in want:
             extras["sweep"] = size_sweep(torch)
         if "capacity" in want:  # opt-in: 163 GB on the device
             extras["capacity"] = capacity_workload(torch)
+        if "tables" in want:  # the paper's Tables 1-2 experiment
+            extras["tables"] = paper_tables(torch)
         if "storage" in want:
             extras.update(extra_workloads(torch, n))
         if "streaming" in want:
