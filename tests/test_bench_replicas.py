@@ -57,3 +57,13 @@ def test_single_process_aggregation():
     b = _bench()
     ms_max, value = b.aggregate_replicas(50.0, cells=10 ** 6, steps=100, world=1)
     assert ms_max == 50.0 and abs(value - 2000.0) < 1e-9
+
+
+def test_cpu_baseline_sample_lasts_at_least_its_bound():
+    """The CPU baseline repeats its oracle calls until the requested seconds
+    of work are timed, and its MLUPS count every update it timed."""
+    b = _bench()
+    mlups, cores, seconds, done = b.cpu_baseline(8, 2, min_seconds=0.3)
+    assert seconds >= 0.3 and done >= 2 and done % 2 == 0
+    assert cores >= 1
+    assert abs(mlups - 8 ** 3 * done / seconds / 1e6) <= 1e-9 * mlups
