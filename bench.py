@@ -292,17 +292,21 @@ def extra_workloads(torch, n, steps=100, warmup=10):
     """Secondary workloads of the same hot path, each timed like the main
     one: the paper's lid-driven cavity (FP32 and 16-bit storage; halfway
     walls, and the on-site walls the paper used, at tau = 0.6 where they
-    are stable)."""
+    are stable), and the FP16 cavity on the tensor-copy staged kernel (a
+    measured alternative to the default two-node kernel)."""
     from paper_1309_1983_gb300.lattice import Lattice
     from paper_1309_1983_gb300 import perfmodel as PM
     out = {}
-    for name, storage, tau, onsite in (("cavity_f32", "f32", 0.55, False),
-                                       ("cavity_f16", "f16", 0.55, False),
-                                       ("cavity_bf16", "bf16", 0.55, False),
-                                       ("cavity_onsite_f32", "f32", 0.6, True),
-                                       ("cavity_onsite_f16", "f16", 0.6, True)):
+    for name, storage, tau, onsite, kernel in (("cavity_f32", "f32", 0.55, False, None),
+                                               ("cavity_f16", "f16", 0.55, False, None),
+                                               ("cavity_bf16", "bf16", 0.55, False, None),
+                                               ("cavity_onsite_f32", "f32", 0.6, True, None),
+                                               ("cavity_onsite_f16", "f16", 0.6, True, None),
+                                               ("cavity_f16_tma", "f16", 0.55, False, "tma")):
         L = Lattice(n, n, n, tau, walls=(True, True, True), lid=(0.05, 0.0, 0.0), storage=storage,
                     onsite=onsite)
+        if kernel:
+            L.set_kernel(kernel)
         L.init_equilibrium()
         L.step(warmup)
         ms, per = timed_steps(L, steps, torch)
@@ -310,7 +314,7 @@ def extra_workloads(torch, n, steps=100, warmup=10):
         eb = 4 if storage == "f32" else 2
         out[name] = {"mlups": round(mlups, 1), "bytes_per_lu": PM.bytes_per_update(eb),
                      "gbs": round(PM.achieved_gbs(mlups, PM.bytes_per_update(eb)), 1),
-                     "steps": steps}
+                     "steps": steps, "kernel": kernel or "x2"}
         L.close()
         del L
         torch.cuda.empty_cache()
